@@ -1,0 +1,139 @@
+"""Seeded synthetic inputs shaped like the paper's workloads (Section 5).
+
+This module holds no arithmetic of the sorting method.  It is the one piece
+shared by the CPU oracle's tests and the GPU path's tests and benchmarks:
+both sort exactly the arrays it returns.  The generators are written in C
+(``gen_inputs.c``, compiled on first use with gcc) so that 2^28-element
+inputs take seconds, not minutes.
+
+Distributions (Section 5): Uniform, Exponential, AlmostSorted, Sorted,
+ReverseSorted, Ones, RootDup, TwoDup, EightDup.  Element types: 64-bit
+unsigned keys, float64 keys, 16-byte (key, payload) pairs, and 100-byte
+records whose first 10 bytes are the key (compared as unsigned bytes).
+The exact definitions and seeds are documented in ``gen_inputs.c``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+DISTRIBUTIONS = (
+    "uniform", "exponential", "almost_sorted", "sorted", "reverse_sorted",
+    "ones", "root_dup", "two_dup", "eight_dup",
+)
+_DIST_ID = {name: i for i, name in enumerate(DISTRIBUTIONS)}
+
+# Seeds: 1 input values, 2 AlmostSorted swaps, 3 payloads, 4 batch lengths,
+# 5 arrival times.
+SEED_VALUES, SEED_SWAPS, SEED_PAYLOAD, SEED_LENGTHS, SEED_ARRIVALS = 1, 2, 3, 4, 5
+
+PAIR_DTYPE = np.dtype([("key", "<u8"), ("payload", "<u8")])
+REC100_DTYPE = np.dtype((np.void, 100))
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gen_inputs.c")
+_LIB = os.path.join(_HERE, "libips4o_inputs.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile gen_inputs.c into an in-tree shared library (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c11", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            u64, u64p, i32 = ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+            lib.gen_splitmix64_at.restype = u64
+            lib.gen_splitmix64_at.argtypes = [u64, u64]
+            for name in ("gen_u64", "gen_f64"):
+                f = getattr(lib, name)
+                f.restype = i32
+                f.argtypes = [u64p, u64, i32, u64]
+            lib.gen_pair.restype = i32
+            lib.gen_pair.argtypes = [u64p, u64, i32, u64, u64]
+            lib.gen_rec100.restype = i32
+            lib.gen_rec100.argtypes = [u64p, u64, i32, u64, u64]
+            lib.gen_log_uniform_lengths.restype = i32
+            lib.gen_log_uniform_lengths.argtypes = [u64p, u64, ctypes.c_double, ctypes.c_double, u64]
+            _lib = lib
+    return _lib
+
+
+def _dist_id(dist: str) -> int:
+    try:
+        return _DIST_ID[dist]
+    except KeyError:
+        raise ValueError(f"unknown distribution {dist!r}; expected one of {DISTRIBUTIONS}") from None
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"{what} failed with code {rc}")
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    """Output i (0-based) of the SplitMix64 stream with the given seed."""
+    return int(_load().gen_splitmix64_at(seed, i))
+
+
+def u64(n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:
+    out = np.empty(n, dtype=np.uint64)
+    _check(_load().gen_u64(out.ctypes.data, n, _dist_id(dist), seed), "gen_u64")
+    return out
+
+
+def f64(n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:
+    out = np.empty(n, dtype=np.float64)
+    _check(_load().gen_f64(out.ctypes.data, n, _dist_id(dist), seed), "gen_f64")
+    return out
+
+
+def pair(n: int, dist: str = "uniform", seed: int = SEED_VALUES,
+         payload_seed: int = SEED_PAYLOAD) -> np.ndarray:
+    out = np.empty(n, dtype=PAIR_DTYPE)
+    _check(_load().gen_pair(out.ctypes.data, n, _dist_id(dist), seed, payload_seed), "gen_pair")
+    return out
+
+
+def rec100(n: int, dist: str = "uniform", seed: int = SEED_VALUES,
+           payload_seed: int = SEED_PAYLOAD) -> np.ndarray:
+    """n records as an (n, 100) uint8 array."""
+    out = np.empty((n, 100), dtype=np.uint8)
+    _check(_load().gen_rec100(out.ctypes.data, n, _dist_id(dist), seed, payload_seed), "gen_rec100")
+    return out
+
+
+def log_uniform_lengths(count: int, lo_log2: float, hi_log2: float,
+                        seed: int = SEED_LENGTHS) -> np.ndarray:
+    """count lengths floor(2^U), U uniform in [lo_log2, hi_log2]."""
+    out = np.empty(count, dtype=np.uint64)
+    _check(_load().gen_log_uniform_lengths(out.ctypes.data, count, lo_log2, hi_log2, seed),
+           "gen_log_uniform_lengths")
+    return out
+
+
+def make(key_type: str, n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:
+    """Inputs by key-type name: 'u64', 'f64', 'pair' or 'rec100'."""
+    if key_type == "u64":
+        return u64(n, dist, seed)
+    if key_type == "f64":
+        return f64(n, dist, seed)
+    if key_type == "pair":
+        return pair(n, dist, seed)
+    if key_type == "rec100":
+        return rec100(n, dist, seed)
+    raise ValueError(f"unknown key type {key_type!r}")
