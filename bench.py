@@ -1,0 +1,327 @@
+"""Benchmark: in-place samplesort of 2^28 uint64 keys on one GB300.
+
+A step is one complete sort (every distribution level and the base case) of
+a fresh copy of the input, which is already resident in HBM; the copy that
+restores the input between steps is not timed.  The input (2 GiB) is larger
+than the 129 MB L2, so no flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dist uniform]
+  python bench.py --impl reference     # the CPU oracle on a bounded sample
+
+Prints one JSON line.  `value` is keys/s over all ranks (N > 1 runs
+independent replicas, one per GPU: the sort does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "keys/s"
+LOG2N = 28
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.path or not os.path.exists(self.path):
+            return out
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]) if parts[3] not in ("[N/A]", "") else 0.0,
+                             parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return out
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        loaded = [r for r in rows if r[2] > 200.0] or rows
+        reasons = set()
+        for r in loaded:
+            for nm, v in zip(names, r[3]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        out.update(sm_mhz=statistics.median(r[0] for r in loaded), sm_max_mhz=max(r[1] for r in rows),
+                   reasons=sorted(reasons), samples=len(rows),
+                   power_w_max=max(r[2] for r in rows))
+        return out
+
+
+def cpu_baseline(log2n_sample: int = 24, reps: int = 1):
+    """The oracle, as it stands, single-threaded on a bounded sample."""
+    import oracle
+    from paper_1705_02257_gb300 import inputs
+    n = 1 << log2n_sample
+    a = inputs.u64(n, "uniform")
+    oracle.sort(a[:1024], "u64")                      # load/build outside the timing
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        oracle.sort(a, "u64")
+    dt = time.perf_counter() - t0
+    return {"value": n * reps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"2^{log2n_sample} uint64 Uniform keys (seed 1), {reps} sort(s), single-threaded C oracle, "
+                      f"{dt:.1f} s", "host_cores": os.cpu_count()}
+
+
+def run_reference(args):
+    rank, world, _ = _dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1705_02257_gb300 import inputs
+    log2s = args.ref_log2n
+    n = 1 << log2s
+    base = inputs.u64(n, args.dist)
+    oracle.sort(base[:1024], "u64")
+    for _ in range(args.warmup):
+        oracle.sort(base, "u64")
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sort(base, "u64")
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = n * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"in-place sort of 2^{LOG2N} uint64 keys, {args.dist} (seed 1); "
+                               f"reference steps sort a 2^{log2s}-key sample",
+                   "n": 1 << LOG2N, "key_type": "u64", "distribution": args.dist},
+        "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
+                         "sample": f"2^{log2s} uint64 {args.dist} keys per step, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = _dist_env()
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1705_02257_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1705_02257_gb300 import inputs, ips4o
+
+    n = 1 << args.log2n
+    host = inputs.u64(n, args.dist)
+    pristine = torch.from_numpy(host.view(np.int64)).cuda()
+    work = torch.empty_like(pristine)
+    stream = torch.cuda.current_stream()
+    ips4o.reset_params()
+
+    def one_step():
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        ips4o.sort(work, "u64")
+        e.record(stream)
+        torch.cuda.synchronize()
+        return s.elapsed_time(e)
+
+    for _ in range(args.warmup):
+        one_step()
+    launches_per_step = ips4o.stats()["kernel_launches"]
+
+    if dist_on:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        for _ in range(args.steps):
+            times.append(one_step())
+    torch.cuda.synchronize()
+    if dist_on:
+        tdist.barrier()
+    total_ms = sum(times)
+    if dist_on:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    stats = ips4o.stats()
+    levels = stats["levels"]
+
+    # output check on the last timed step: sorted and a permutation
+    out = work.cpu().numpy().view(np.uint64)
+    sorted_ok = bool(np.all(out[1:] >= out[:-1]))
+
+    # per-kernel times (CUDA events around each launch on the sort's stream)
+    ips4o.set_params(profile=1)
+    prof_steps = max(1, min(3, args.steps))
+    phase_ms = {p: 0.0 for p in ips4o.PHASES}
+    phase_launches = {p: 0 for p in ips4o.PHASES}
+    for _ in range(prof_steps):
+        one_step()
+        st = ips4o.stats()
+        for p in ips4o.PHASES:
+            phase_ms[p] += st["phase_ms"][p]
+            phase_launches[p] += st["phase_launches"][p]
+    ips4o.reset_params()
+    elem = 8
+    # algorithmic bytes per launch (Appendix B I/O volume): classification and
+    # block permutation each read and write the elements of the launch once.
+    per_level = 2.0 * n * elem * levels * prof_steps
+    alg = {
+        "classify": per_level,
+        "block_permutation": per_level,
+        "cleanup_base_case": 2.0 * n * elem * prof_steps,
+    }
+    dominant = max(alg, key=lambda p: phase_ms[p])
+    peak, peak_kind = _peaks()
+    achieved = alg[dominant] / (phase_ms[dominant] * 1e-3) / 1e9 if phase_ms[dominant] > 0 else None
+    ms_per_step = total_ms / args.steps
+    value = n * world * args.steps / (total_ms * 1e-3)
+    alg_sort = (4 * levels + 2) * n * elem
+    sort_frac = alg_sort / (ms_per_step * 1e-3) / 1e9 / peak
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_in = torch.from_numpy(host.view(np.int64)).pin_memory()
+        h_work = torch.empty_like(h_in).pin_memory()
+        e2e_times = []
+        for i in range(args.warmup + args.steps):
+            h_work.copy_(h_in)
+            t0 = time.perf_counter()
+            rc = ips4o.ips4o_sort_host(h_work.data_ptr(), n, ips4o.U64, stream.cuda_stream)
+            dt = time.perf_counter() - t0
+            if rc:
+                raise ips4o.Ips4oError(rc, "ips4o_sort_host")
+            if i >= args.warmup:
+                e2e_times.append(dt)
+        e2e_total = sum(e2e_times)
+        if dist_on:
+            t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_total = float(t.item())
+        e2e = {"value": n * world * args.steps / e2e_total, "unit": METRIC,
+               "h2d_bytes_per_step": n * elem, "d2h_bytes_per_step": n * elem,
+               "ms_per_step": 1e3 * e2e_total / args.steps, "host_memory": "pinned"}
+
+    if rank != 0:
+        if dist_on:
+            tdist.destroy_process_group()
+        return 0
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.cpu_log2n)
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"in-place sort of 2^{args.log2n} uint64 keys, {args.dist} (seed 1)",
+                   "n": n, "key_type": "u64", "distribution": args.dist,
+                   "l2": "input 2 GiB per step, larger than the 129 MB L2 (no flush needed)",
+                   "parallelism": f"replicas x{world}", "levels": levels},
+        "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s",
+                     "frac": (achieved / peak) if achieved else None,
+                     "traffic": None,
+                     "alg_bytes_per_launch": alg[dominant] / max(1, phase_launches[dominant]),
+                     "launches": phase_launches[dominant] // prof_steps,
+                     "sort_alg_bytes": alg_sort, "sort_frac": sort_frac},
+        "phase_ms_per_step": {p: phase_ms[p] / prof_steps for p in ips4o.PHASES},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": launches_per_step * args.steps,
+        "output_sorted": sorted_ok,
+        "stats": {k: stats[k] for k in ("levels", "chunks", "subproblems", "blocks_moved", "blocks_skipped",
+                                        "fix_blocks_moved", "base_case_buckets", "workspace_bytes")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        tdist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dist", default="uniform")
+    ap.add_argument("--log2n", type=int, default=LOG2N)
+    ap.add_argument("--ref-log2n", type=int, default=22)
+    ap.add_argument("--cpu-log2n", type=int, default=24)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,156 @@
+/*
+ * ips4o.h — C ABI of the GB300 in-place samplesort library (libips4o_gb300.so).
+ *
+ * The library sorts an array that lives in GPU memory, in place, by the
+ * method of "In-place Parallel Super Scalar Samplesort" (Axtmann, Witt,
+ * Ferizovic, Sanders, 2017): recursive distribution steps of sampling,
+ * local classification into blocks, block permutation and cleanup
+ * (Section 4), with equality buckets for repeated keys (Section 4.4), down
+ * to a base case sorted in on-chip shared memory (Section 4.7).
+ *
+ * Problem statement (Section 1): rearrange A[0..n) so that the keys are
+ * non-decreasing under a total order.  The result's key sequence is unique;
+ * elements with equal keys (and different payloads) may come out in any
+ * order, since the method is not stable.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are device pointers (cudaMalloc, torch CUDA tensors);
+ *     h_* are host pointers.  The caller owns all of them; the library never
+ *     frees or keeps them after the call returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it.
+ *   - The library owns a per-device workspace (see ips4o_workspace_bytes),
+ *     allocated on first use with cudaMalloc and reused; its size is
+ *     O(k*b*t + number of subproblems) as in Theorem 2, plus a small host
+ *     staging area.
+ *   - Calls on the same device are serialised by the library (one workspace
+ *     per device).  They are not capturable in a CUDA graph: the host driver
+ *     reads the number of subproblems of each recursion level back from the
+ *     device before it launches the next level.
+ *   - Return codes: argument errors are detected before any work is queued;
+ *     device-side errors (an exhausted bounded wait, a broken internal
+ *     invariant) are reported by the call that detects them through the
+ *     device status word, which is read at each level.
+ */
+#ifndef IPS4O_GB300_H
+#define IPS4O_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Element types (Section 5 lists 64-bit floating point elements, Pair,
+ * Quartet and 100Bytes records; this library also sorts plain uint64). */
+typedef enum {
+    IPS4O_U64 = 0,         /* 8-byte unsigned integer, natural order; 8-byte aligned */
+    IPS4O_F64 = 1,         /* 8-byte IEEE double, ordered by '<'; the bit pattern b is
+                              ordered as (b has sign) ? ~b : b | 2^63, a total order that
+                              equals '<' on non-NaN values and puts -0.0 before +0.0 */
+    IPS4O_PAIR_U64 = 2,    /* 16-byte {uint64 key; uint64 payload}, ordered by key; 16-byte aligned */
+    IPS4O_REC100_K10 = 3   /* 100-byte record, key = bytes [0,10) compared as unsigned bytes
+                              (lexicographic), payload = bytes [10,100); 4-byte aligned */
+} ips4o_key_type;
+
+typedef enum {
+    IPS4O_OK = 0,
+    IPS4O_ERR_INVALID_ARG = 1,      /* null pointer with n > 0, bad sizes or parameters */
+    IPS4O_ERR_UNSUPPORTED_TYPE = 2, /* key type not one of ips4o_key_type */
+    IPS4O_ERR_MISALIGNED = 3,       /* pointer not aligned as the key type requires */
+    IPS4O_ERR_OOM = 4,              /* workspace could not be allocated */
+    IPS4O_ERR_CUDA = 5,             /* a CUDA runtime call failed (see ips4o_last_cuda_error) */
+    IPS4O_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
+    IPS4O_ERR_INTERNAL = 7,         /* a device-side invariant check failed */
+    IPS4O_ERR_TOO_LARGE = 8         /* request exceeds a fixed capacity of the entry point */
+} ips4o_status;
+
+/* Tuning parameters (Section 4.7 gives k <= 256, alpha = 0.2 log n,
+ * beta = 1, n0 = 16 and b = 2 KiB for its CPUs; the GPU defaults differ and
+ * are explained in the design doc of the source distribution). */
+typedef struct {
+    int k_max;            /* maximum buckets per distribution step, power of two in [4, 256]; default 256 */
+    int alpha;            /* oversampling factor; <= 0 selects the default (max(8, 0.2 log2 n) ... see source) */
+    int base_case_max;    /* buckets of at most this many elements are sorted in shared memory
+                             (clamped to the per-type capacity); <= 0 selects the default */
+    int stripes_per_sm;   /* stripes (local-classification work items) per SM for a level; default 2 */
+    int profile;          /* 1: time every kernel with CUDA events into ips4o_stats.phase_ms */
+    uint64_t seed;        /* sampling seed */
+} ips4o_params;
+
+/* Counters of the last completed call on the calling thread's current device. */
+#define IPS4O_NUM_PHASES 8
+typedef struct {
+    uint64_t n;                    /* elements sorted by the last call */
+    uint32_t levels;               /* distribution levels executed (deepest level reached) */
+    uint32_t chunks;               /* level chunks launched (groups of subproblems) */
+    uint64_t subproblems;          /* distribution steps performed */
+    uint64_t kernel_launches;      /* kernels this library launched for the call */
+    uint64_t blocks_moved;         /* block writes of the block permutation (Section 4.2) */
+    uint64_t blocks_skipped;       /* blocks found already in their bucket and left in place */
+    uint64_t fix_blocks_moved;     /* blocks moved by the empty-block movement (Appendix A) */
+    uint64_t base_case_buckets;    /* buckets sorted by the shared-memory base case */
+    uint64_t elements_distributed; /* sum over levels of the elements classified */
+    uint64_t workspace_bytes;      /* device workspace held by the library on this device */
+    double phase_ms[IPS4O_NUM_PHASES]; /* with params.profile: summed kernel time per phase:
+                                      0 sample, 1 classify, 2 prefix, 3 empty-block fix,
+                                      4 block permutation, 5 cleanup + base case,
+                                      6 standalone base case, 7 other */
+    uint64_t phase_launches[IPS4O_NUM_PHASES];
+} ips4o_stats;
+
+/* Sort d_ptr[0..n) in place (Section 4: recursive distribution steps down
+ * to the base case).  n in {0, 1} is a no-op.  Synchronises the stream once
+ * per recursion level; on return the sort has completed on the device. */
+ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream);
+
+/* Same as ips4o_sort but for an array in HOST memory: copies it to the
+ * device, sorts, and copies the result back (all on `stream`).  The device
+ * staging buffer is owned by the library and kept for reuse. */
+ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream);
+
+/* One distribution step (Section 4: sampling, local classification, block
+ * permutation, cleanup) on d_ptr[0..n), n > base case, leaving the array
+ * partitioned into buckets, followed by nothing else.  Outputs (host):
+ *   h_bounds[0..*num_buckets]  bucket boundaries (h_bounds[0] = 0, last = n),
+ *                              capacity 257 entries;
+ *   h_splitters[0..*num_splitters) the splitter keys of the step in the
+ *                              library's comparable form (u64: the value;
+ *                              f64: the mapped bits; pair: the key), capacity 256;
+ *   *eq                        1 if equality buckets were used (Section 4.4):
+ *                              bucket 2i+1 then holds the keys equal to
+ *                              splitter i, bucket 2i those strictly between
+ *                              splitters i-1 and i.
+ * Splitters are padded to a power-of-two tree by repeating the largest one,
+ * so some buckets are empty. */
+ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream,
+                             uint64_t* h_bounds, size_t* num_buckets,
+                             uint64_t* h_splitters, size_t* num_splitters, int* eq);
+
+/* Device workspace the library needs for a sort of n elements of the type. */
+size_t ips4o_workspace_bytes(size_t n, int key_type);
+
+/* Free the workspace and staging buffers held on the current device. */
+ips4o_status ips4o_release_workspace(void);
+
+/* Parameters (process-wide).  ips4o_set_params(NULL) restores defaults. */
+ips4o_status ips4o_set_params(const ips4o_params* p);
+ips4o_status ips4o_get_params(ips4o_params* out);
+
+/* Counters of the last call made by this process on the current device. */
+ips4o_status ips4o_get_stats(ips4o_stats* out);
+
+/* Capacity of the shared-memory base case for a key type, in elements. */
+size_t ips4o_base_case_capacity(int key_type);
+
+const char* ips4o_status_string(int status);
+
+/* Text of the last CUDA error seen by the library (empty if none). */
+const char* ips4o_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IPS4O_GB300_H */

@@ -1,0 +1,247 @@
+// ips4o_api.cu — the extern "C" entry points declared in include/ips4o.h.
+//
+// Argument checking, per-device state (workspace, pinned staging, stats),
+// and dispatch on the element type to the per-type drivers.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "ips4o_common.cuh"
+#include "ips4o_host.h"
+
+namespace ips4o {
+
+namespace {
+std::mutex g_mtx;
+DeviceState* g_states[64] = {nullptr};
+ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
+thread_local char g_last_err[256] = {0};
+}  // namespace
+
+ips4o_params& global_params() { return g_params; }
+
+void set_last_cuda_error(cudaError_t e, const char* where) {
+    std::snprintf(g_last_err, sizeof g_last_err, "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
+}
+
+DeviceState* current_device_state(cudaError_t* err) {
+    int dev = 0;
+    *err = cudaGetDevice(&dev);
+    if (*err != cudaSuccess) return nullptr;
+    if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
+    std::lock_guard<std::mutex> lk(g_mtx);
+    if (!g_states[dev]) {
+        DeviceState* s = new DeviceState();
+        s->device = dev;
+        *err = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
+        if (*err != cudaSuccess) { delete s; return nullptr; }
+        g_states[dev] = s;
+    }
+    return g_states[dev];
+}
+
+ips4o_status ensure_device_buffer(void** ptr, size_t* have, size_t need) {
+    if (*ptr && *have >= need) return IPS4O_OK;
+    if (*ptr) {
+        cudaError_t e = cudaFree(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+        if (e != cudaSuccess) { set_last_cuda_error(e, "cudaFree"); return IPS4O_ERR_CUDA; }
+    }
+    cudaError_t e = cudaMalloc(ptr, need);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_last_cuda_error(e, "cudaMalloc(workspace)");
+        return e == cudaErrorMemoryAllocation ? IPS4O_ERR_OOM : IPS4O_ERR_CUDA;
+    }
+    *have = need;
+    return IPS4O_OK;
+}
+
+ips4o_status ensure_host_pinned(void** ptr, size_t* have, size_t need) {
+    if (*ptr && *have >= need) return IPS4O_OK;
+    if (*ptr) {
+        cudaFreeHost(*ptr);
+        *ptr = nullptr;
+        *have = 0;
+    }
+    cudaError_t e = cudaMallocHost(ptr, need);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_last_cuda_error(e, "cudaMallocHost(staging)");
+        return IPS4O_ERR_OOM;
+    }
+    *have = need;
+    return IPS4O_OK;
+}
+
+static size_t elem_size(int kt) {
+    switch (kt) {
+    case IPS4O_U64: return 8;
+    case IPS4O_F64: return 8;
+    case IPS4O_PAIR_U64: return 16;
+    default: return 0;
+    }
+}
+
+static ips4o_status check_args(const void* p, size_t n, int kt) {
+    if (kt < 0 || kt > IPS4O_REC100_K10) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (elem_size(kt) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (n > 1 && !p) return IPS4O_ERR_INVALID_ARG;
+    if (n > ((size_t)1 << 37)) return IPS4O_ERR_TOO_LARGE;   // block indices must fit 31 bits
+    if (p && ((uintptr_t)p % elem_size(kt)) != 0) return IPS4O_ERR_MISALIGNED;
+    return IPS4O_OK;
+}
+
+static ips4o_status dispatch(DeviceState& st, void* d, size_t n, int kt, cudaStream_t s, PartitionOut* part) {
+    switch (kt) {
+    case IPS4O_U64: return sort_u64(st, d, n, s, part);
+    case IPS4O_F64: return sort_f64(st, d, n, s, part);
+    case IPS4O_PAIR_U64: return sort_pair(st, d, n, s, part);
+    default: return IPS4O_ERR_UNSUPPORTED_TYPE;
+    }
+}
+
+}  // namespace ips4o
+
+using namespace ips4o;
+
+extern "C" {
+
+ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream) {
+    ips4o_status rc = check_args(d_ptr, n, key_type);
+    if (rc != IPS4O_OK) return rc;
+    if (n < 2) return IPS4O_OK;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    return dispatch(*st, d_ptr, n, key_type, (cudaStream_t)stream, nullptr);
+}
+
+ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) {
+    ips4o_status rc = check_args(h_ptr, n, key_type);
+    if (rc != IPS4O_OK) return rc;
+    if (n < 2) return IPS4O_OK;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    const size_t bytes = n * elem_size(key_type);
+    rc = ensure_device_buffer(&st->d_host_copy, &st->d_host_copy_bytes, bytes);
+    if (rc != IPS4O_OK) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemcpyAsync(st->d_host_copy, h_ptr, bytes, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(H2D)"); return IPS4O_ERR_CUDA; }
+    rc = dispatch(*st, st->d_host_copy, n, key_type, s, nullptr);
+    if (rc != IPS4O_OK) return rc;
+    e = cudaMemcpyAsync(h_ptr, st->d_host_copy, bytes, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(D2H)"); return IPS4O_ERR_CUDA; }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamSynchronize"); return IPS4O_ERR_CUDA; }
+    return IPS4O_OK;
+}
+
+ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream, uint64_t* h_bounds,
+                             size_t* num_buckets, uint64_t* h_splitters, size_t* num_splitters, int* eq) {
+    ips4o_status rc = check_args(d_ptr, n, key_type);
+    if (rc != IPS4O_OK) return rc;
+    if (n < 2 || !h_bounds || !num_buckets || !h_splitters || !num_splitters || !eq) return IPS4O_ERR_INVALID_ARG;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    PartitionOut out{h_bounds, num_buckets, h_splitters, num_splitters, eq};
+    return dispatch(*st, d_ptr, n, key_type, (cudaStream_t)stream, &out);
+}
+
+size_t ips4o_workspace_bytes(size_t n, int key_type) {
+    int sms = 152;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (st) sms = st->sms;
+    else cudaGetLastError();
+    switch (key_type) {
+    case IPS4O_U64: return workspace_bytes_u64(n, sms);
+    case IPS4O_F64: return workspace_bytes_f64(n, sms);
+    case IPS4O_PAIR_U64: return workspace_bytes_pair(n, sms);
+    default: return 0;
+    }
+}
+
+ips4o_status ips4o_release_workspace(void) {
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    if (st->d_ws) cudaFree(st->d_ws);
+    if (st->d_host_copy) cudaFree(st->d_host_copy);
+    if (st->h_stage) cudaFreeHost(st->h_stage);
+    for (cudaEvent_t ev : st->events) cudaEventDestroy(ev);
+    st->events.clear();
+    st->d_ws = st->d_host_copy = st->h_stage = nullptr;
+    st->ws_bytes = st->d_host_copy_bytes = st->h_stage_bytes = 0;
+    return IPS4O_OK;
+}
+
+ips4o_status ips4o_set_params(const ips4o_params* p) {
+    std::lock_guard<std::mutex> lk(g_mtx);
+    if (!p) {
+        g_params = ips4o_params{256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
+        return IPS4O_OK;
+    }
+    if (p->k_max < 4 || p->k_max > 256 || (p->k_max & (p->k_max - 1)) != 0) return IPS4O_ERR_INVALID_ARG;
+    if (p->stripes_per_sm < 1 || p->stripes_per_sm > 16) return IPS4O_ERR_INVALID_ARG;
+    if (p->alpha > 4095) return IPS4O_ERR_INVALID_ARG;
+    g_params = *p;
+    return IPS4O_OK;
+}
+
+ips4o_status ips4o_get_params(ips4o_params* out) {
+    if (!out) return IPS4O_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mtx);
+    *out = g_params;
+    return IPS4O_OK;
+}
+
+ips4o_status ips4o_get_stats(ips4o_stats* out) {
+    if (!out) return IPS4O_ERR_INVALID_ARG;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    *out = st->stats;
+    return IPS4O_OK;
+}
+
+size_t ips4o_base_case_capacity(int key_type) {
+    switch (key_type) {
+    case IPS4O_U64: return TU64::kBaseCap;
+    case IPS4O_F64: return TF64::kBaseCap;
+    case IPS4O_PAIR_U64: return TPair::kBaseCap;
+    default: return 0;
+    }
+}
+
+const char* ips4o_status_string(int s) {
+    switch (s) {
+    case IPS4O_OK: return "ok";
+    case IPS4O_ERR_INVALID_ARG: return "invalid argument";
+    case IPS4O_ERR_UNSUPPORTED_TYPE: return "unsupported key type";
+    case IPS4O_ERR_MISALIGNED: return "pointer not aligned for the key type";
+    case IPS4O_ERR_OOM: return "out of memory";
+    case IPS4O_ERR_CUDA: return "CUDA error";
+    case IPS4O_ERR_TIMEOUT: return "bounded device wait timed out";
+    case IPS4O_ERR_INTERNAL: return "internal invariant violated";
+    case IPS4O_ERR_TOO_LARGE: return "request exceeds a fixed capacity";
+    default: return "unknown status";
+    }
+}
+
+const char* ips4o_last_cuda_error(void) { return g_last_err; }
+
+}  // extern "C"

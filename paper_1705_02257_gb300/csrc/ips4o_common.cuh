@@ -1,0 +1,248 @@
+// ips4o_common.cuh — element traits, workspace layout and device primitives
+// shared by the distribution-step kernels.
+//
+// Terminology follows the paper (Sections 3 and 4): k buckets per step,
+// blocks of b elements, stripes (one per local-classification work item,
+// the GPU counterpart of a thread's stripe), delimiters d_i, write/read
+// pointers w_i and r_i, overflow block, equality buckets.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ips4o {
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+constexpr int kMaxBuckets = 256;      // buckets per step (ids fit one byte)
+constexpr int kMaxLeaves = 256;       // leaves of the implicit search tree
+constexpr int kMaxStripesPerSub = 1024;
+constexpr u32 kPtrBias = 0x80000000u; // r_i is stored biased so it may go below w_i - 1
+
+// Device status word bits.
+constexpr u32 kStatusTimeout = 1u;     // a bounded wait gave up
+constexpr u32 kStatusInternal = 2u;    // an invariant check failed
+constexpr u32 kStatusCapacity = 4u;    // a fixed-capacity list overflowed
+
+// ---------------------------------------------------------------- traits
+// Each element type defines its storage type, its comparable key and the
+// block size b in elements.  The paper uses b = max(1, 2^floor(11 - log2 s))
+// (about 2 KiB) for CPU caches; here a block is 512 bytes so that the k
+// per-bucket buffer blocks of a classification CTA fit in shared memory.
+
+struct TU64 {
+    typedef u64 elem_t;
+    typedef u64 key_t;
+    static constexpr int kId = 0;
+    static constexpr int kBlock = 64;                 // 64 x 8 B = 512 B
+    static constexpr int kBaseCap = 8192;              // shared-memory base case capacity
+    __host__ __device__ static inline key_t key(const elem_t& e) { return e; }
+    __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+};
+
+struct TF64 {
+    typedef u64 elem_t;     // raw IEEE bits
+    typedef u64 key_t;      // order-preserving map of the bits
+    static constexpr int kId = 1;
+    static constexpr int kBlock = 64;
+    static constexpr int kBaseCap = 8192;
+    __host__ __device__ static inline key_t key(const elem_t& e) {
+        return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
+    }
+    __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+};
+
+struct alignas(16) PairElem {
+    u64 k;
+    u64 p;
+};
+
+struct TPair {
+    typedef PairElem elem_t;
+    typedef u64 key_t;
+    static constexpr int kId = 2;
+    static constexpr int kBlock = 32;                 // 32 x 16 B = 512 B
+    static constexpr int kBaseCap = 4096;
+    __host__ __device__ static inline key_t key(const elem_t& e) { return e.k; }
+    __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+};
+
+// ------------------------------------------------------------ descriptors
+// One subproblem (a bucket of the previous level, or the whole input) of a
+// chunk of work at one recursion level.
+struct SubDesc {
+    u64 begin;          // absolute element offset
+    u64 n;              // elements
+    u32 stripe_begin;   // first stripe in the chunk's stripe table
+    u32 num_stripes;
+    u32 k_target;       // planned number of leaves (power of two)
+    u32 alpha;          // oversampling factor
+    u32 level;
+    // written by the sampling kernel
+    u32 log_leaves;
+    u32 eq;             // equality buckets on
+    u32 nbuckets;       // leaves, or 2*leaves - 1 with equality buckets
+    // written by the prefix kernel
+    u64 blocks_total;   // full blocks produced by local classification
+};
+
+struct StripeDesc {
+    u64 begin;          // absolute element index; (begin - sub.begin) % b == 0
+    u64 end;
+    u64 pool_off;       // element offset of this stripe's leftover area
+    u32 sub;            // index of the subproblem in the chunk
+    u32 pool_cap;
+};
+
+struct Task {           // a subproblem emitted for the next level
+    u64 begin;
+    u64 n;
+};
+
+struct FixItem {        // a bucket region whose empty blocks must be moved (Appendix A)
+    u32 sub;
+    u32 bucket;
+};
+
+// Device-side counters of one chunk.
+struct ChunkCounters {
+    u32 stripe_next;    // dynamic stripe scheduler for classification
+    u32 fix_count;      // entries in the fix list
+    u32 ticket;         // cleanup ticket dispenser
+    u32 next_count;     // tasks emitted for the next level
+    u32 status;         // error bits
+    u32 pad[3];
+    u64 blocks_moved;
+    u64 blocks_skipped;
+    u64 fix_blocks;
+    u64 base_buckets;
+};
+
+// Pointers into the workspace for one key type.
+template <class T>
+struct Workspace {
+    typedef typename T::elem_t elem_t;
+    typedef typename T::key_t key_t;
+    SubDesc* subs;            // [max_sub]
+    StripeDesc* stripes;      // [max_stripes]
+    key_t* tree;              // [max_sub][256]   implicit search tree a[1..L-1]
+    key_t* spl;               // [max_sub][256]   sorted splitters s_1..s_{L-1}
+    u64* bstart;              // [max_sub][257]   bucket starts relative to sub begin
+    u32* delim;               // [max_sub][257]   delimiter block indices d_i
+    u64* wr;                  // [max_sub][256]   packed (w_i << 32) | (r_i + bias)
+    u32* readers;             // [max_sub][256]   threads currently reading from bucket i
+    u32* flags;               // [max_sub][256]   cleanup hand-over flags
+    u32* region_full;         // [max_sub][256]   full blocks inside region [d_i, d_{i+1})
+    u32* bucket_full;         // [max_sub][256]   full blocks of bucket i (all stripes)
+    u32* counts;              // [max_stripes][256] elements per bucket per stripe
+    u32* lscan;               // [max_stripes][256] leftover offset per bucket in the stripe area
+    u32* stripe_full;         // [max_stripes]     full blocks flushed by the stripe
+    FixItem* fix_list;        // [max_sub * 256]
+    elem_t* pool;             // [pool_cap]        partially filled buffer blocks (leftovers)
+    elem_t* overflow;         // [max_sub][b]      overflow block per subproblem
+    Task* next_tasks;         // [next_cap]
+    ChunkCounters* ctr;       // [1]
+    u32 max_sub, max_stripes;
+    u64 pool_cap, next_cap;
+};
+
+// ------------------------------------------------------------ primitives
+__device__ __forceinline__ u32 smem_addr(const void* p) {
+    return (u32)__cvta_generic_to_shared(p);
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem);
+
+template <>
+__device__ __forceinline__ void cp_async<8>(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(smem)), "l"(gmem)
+                 : "memory");
+}
+template <>
+__device__ __forceinline__ void cp_async<16>(void* smem, const void* gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ u64 atom_add_acq_rel(u64* p, u64 v) {
+    u64 old;
+    asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ u32 ld_acquire(const u32* p) {
+    u32 v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(u32* p, u32 v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_relaxed(u32* p, u32 v) {
+    asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ u64 mix64(u64 z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__host__ __device__ __forceinline__ u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ void set_status(ChunkCounters* c, u32 bits) { atomicOr(&c->status, bits); }
+
+// Bucket of key e (Section 3): descend the implicit tree a[1..L-1]
+// (a_1 = s_{L/2}, children of a_j are a_{2j}, a_{2j+1}) with j = 2j + (a_j <= e);
+// the leaf index j - L is the number of splitters <= e, so that
+// s_i <= e < s_{i+1}.  With equality buckets (Section 4.4) one more
+// comparison against s_i separates the keys equal to s_i (bucket 2i-1)
+// from those strictly between s_i and s_{i+1} (bucket 2i).
+template <class K>
+__device__ __forceinline__ int classify_key(const K& e, const K* tree, const K* spl, int log_leaves, bool eq) {
+    int j = 1;
+#pragma unroll
+    for (int l = 0; l < 8; ++l)
+        if (l < log_leaves) j = 2 * j + (tree[j] <= e ? 1 : 0);
+    int i = j - (1 << log_leaves);
+    if (!eq) return i;
+    return 2 * i - ((i > 0 && spl[i] == e) ? 1 : 0);
+}
+
+// Block-wide exclusive scan of one value per thread for the first
+// `count` threads (count <= blockDim.x, blockDim.x multiple of 32).
+// Returns the exclusive prefix; *total receives the sum.  Uses `tmp`
+// (>= 32 entries) of shared memory and two __syncthreads.
+template <typename V>
+__device__ __forceinline__ V block_exclusive_scan(V v, V* tmp, V* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    V x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        V y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) tmp[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        V t = lane < nwarps ? tmp[lane] : V(0);
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            V y = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += y;
+        }
+        tmp[lane] = t;   // inclusive warp totals
+    }
+    __syncthreads();
+    V warp_prefix = warp > 0 ? tmp[warp - 1] : V(0);
+    *total = tmp[nwarps - 1];
+    return warp_prefix + x - v;
+}
+
+}  // namespace ips4o

@@ -1,0 +1,405 @@
+// ips4o_driver.cuh — host driver of the recursion (Section 4: "As long as
+// problems with at least beta*n/t elements exist, we partition those ...").
+//
+// The driver keeps the list of subproblems of the current recursion level on
+// the host.  A level is processed in chunks (groups of subproblems whose
+// state fits the workspace); each chunk is one launch of the six
+// distribution-step kernels on the caller's stream, after which the buckets
+// larger than the base case come back as the next level's subproblems and
+// the others have already been sorted in shared memory by the cleanup kernel.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "ips4o_host.h"
+#include "ips4o_kernels.cuh"
+
+namespace ips4o {
+
+constexpr u32 kSpinLimit = 1u << 22;     // bounded waits: ~0.3 s with the sleeps
+constexpr int kDefaultAlpha = 16;
+constexpr u64 kMinStripe = 1u << 16;     // elements; keeps leftovers small relative to a stripe
+
+inline u32 pow2_ceil_host(u64 x) {
+    u32 p = 1;
+    while (p < x && p < (1u << 30)) p <<= 1;
+    return p;
+}
+
+template <class T>
+struct Caps {
+    u32 max_sub, max_stripes;
+    u64 pool_cap, next_cap;
+};
+
+template <class T>
+Caps<T> caps_for(u64 n, int sms, int stripes_per_sm) {
+    const u64 B = T::kBlock, cap = T::kBaseCap;
+    Caps<T> c;
+    u64 target = (u64)std::max(1, stripes_per_sm) * (u64)std::max(1, sms);
+    c.max_sub = (u32)std::min<u64>(1024, n / (cap + 1) + 1);
+    c.max_stripes = (u32)std::min<u64>(4096, target + c.max_sub + 1);
+    target = std::min<u64>(target, n / kMinStripe + 1);   // stripes are at least kMinStripe long
+    u64 pool = std::max<u64>(n / 32, target * kMaxBuckets * (B - 1));
+    pool = std::min<u64>(pool, n + kMaxBuckets * B);
+    c.pool_cap = std::max<u64>(pool, (u64)kMaxBuckets * B);
+    c.next_cap = n / (cap + 1) + 16;
+    return c;
+}
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Workspace carving: returns total bytes; fills ws when base != nullptr.
+template <class T>
+size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char* {
+        off = align_up(off, 256);
+        char* p = base ? base + off : nullptr;
+        off += bytes;
+        return p;
+    };
+    const u64 S = c.max_sub, R = c.max_stripes;
+    Workspace<T> w;
+    w.subs = (SubDesc*)take(S * sizeof(SubDesc));
+    w.stripes = (StripeDesc*)take(R * sizeof(StripeDesc));
+    w.tree = (K*)take(S * kMaxLeaves * sizeof(K));
+    w.spl = (K*)take(S * kMaxLeaves * sizeof(K));
+    w.bstart = (u64*)take(S * (kMaxBuckets + 1) * 8);
+    w.delim = (u32*)take(S * (kMaxBuckets + 1) * 4);
+    w.wr = (u64*)take(S * kMaxBuckets * 8);
+    w.readers = (u32*)take(S * kMaxBuckets * 4);
+    w.flags = (u32*)take(S * kMaxBuckets * 4);
+    w.region_full = (u32*)take(S * kMaxBuckets * 4);
+    w.bucket_full = (u32*)take(S * kMaxBuckets * 4);
+    w.counts = (u32*)take(R * kMaxBuckets * 4);
+    w.lscan = (u32*)take(R * kMaxBuckets * 4);
+    w.stripe_full = (u32*)take(R * 4);
+    w.fix_list = (FixItem*)take(S * kMaxBuckets * sizeof(FixItem));
+    w.pool = (E*)take(c.pool_cap * sizeof(E));
+    w.overflow = (E*)take(S * T::kBlock * sizeof(E));
+    w.next_tasks = (Task*)take(c.next_cap * sizeof(Task));
+    w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
+    w.max_sub = c.max_sub;
+    w.max_stripes = c.max_stripes;
+    w.pool_cap = c.pool_cap;
+    w.next_cap = c.next_cap;
+    if (ws) *ws = w;
+    return align_up(off, 256);
+}
+
+// Pinned host staging: SubDesc[max_sub] + StripeDesc[max_stripes] +
+// ChunkCounters + Task[next_cap].
+template <class T>
+size_t host_stage_bytes(const Caps<T>& c) {
+    return align_up(c.max_sub * sizeof(SubDesc), 256) + align_up(c.max_stripes * sizeof(StripeDesc), 256) +
+           align_up(sizeof(ChunkCounters), 256) + align_up(c.next_cap * sizeof(Task), 256);
+}
+
+template <class T>
+size_t workspace_bytes_t(size_t n, int sms) {
+    Caps<T> c = caps_for<T>(n, sms, global_params().stripes_per_sm);
+    return carve<T>(c, nullptr, nullptr);
+}
+
+// Number of leaves for a subproblem of n elements (Section 4.7, adaptive k
+// on the last two levels): the reduction 2n/T to reach half the base-case
+// capacity T is taken in one step when k_max allows, split evenly over two
+// steps when k_max^2 allows, and k_max is used otherwise.
+inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
+    const double r = 2.0 * (double)n / (double)base_cap;
+    u32 k;
+    if (r <= (double)k_max) k = pow2_ceil_host((u64)std::ceil(r));
+    else if (r <= (double)k_max * (double)k_max) k = pow2_ceil_host((u64)std::ceil(std::sqrt(r)));
+    else k = k_max;
+    return std::min(std::max<u32>(k, 4), k_max);
+}
+
+#define IPS4O_CUDA(call)                                    \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) {                            \
+            set_last_cuda_error(e_, #call);                 \
+            return IPS4O_ERR_CUDA;                          \
+        }                                                   \
+    } while (0)
+
+template <class T>
+struct Driver {
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
+
+    DeviceState& st;
+    cudaStream_t stream;
+    const ips4o_params prm;
+    Workspace<T> ws;
+    Caps<T> caps;
+    SubDesc* h_subs;
+    StripeDesc* h_stripes;
+    ChunkCounters* h_ctr;
+    Task* h_tasks;
+    u32 base_cap;
+    u32 k_max;
+    int permute_grid = 0;
+    int next_event = 0;
+    struct Timed { int phase; int ev; };
+    std::vector<Timed> timed;
+
+    Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
+
+    ips4o_status setup(u64 n) {
+        caps = caps_for<T>(n, st.sms, prm.stripes_per_sm);
+        const size_t need = carve<T>(caps, nullptr, nullptr);
+        ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
+        if (rc != IPS4O_OK) return rc;
+        carve<T>(caps, (char*)st.d_ws, &ws);
+        rc = ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(caps));
+        if (rc != IPS4O_OK) return rc;
+        char* h = (char*)st.h_stage;
+        h_subs = (SubDesc*)h;
+        h += align_up(caps.max_sub * sizeof(SubDesc), 256);
+        h_stripes = (StripeDesc*)h;
+        h += align_up(caps.max_stripes * sizeof(StripeDesc), 256);
+        h_ctr = (ChunkCounters*)h;
+        h += align_up(sizeof(ChunkCounters), 256);
+        h_tasks = (Task*)h;
+        base_cap = (u32)T::kBaseCap;
+        if (prm.base_case_max > 0) base_cap = std::min<u32>(base_cap, (u32)std::max(prm.base_case_max, 16));
+        k_max = (u32)std::min(256, std::max(4, prm.k_max));
+        k_max = pow2_ceil_host(k_max);
+        if (k_max > 256) k_max = 256;
+        IPS4O_CUDA(cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)ClassifyCfg<T>::smem_bytes));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)CleanupCfg<T>::smem_bytes));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(T::kBaseCap * sizeof(E))));
+        int occ = 0;
+        IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB, 0));
+        permute_grid = std::max(1, occ) * st.sms;
+        st.stats = ips4o_stats{};
+        st.stats.workspace_bytes = st.ws_bytes;
+        return IPS4O_OK;
+    }
+
+    // --- profiling helpers: events around launches when prm.profile is set
+    ips4o_status ev_begin(int phase, int* slot) {
+        *slot = -1;
+        if (!prm.profile) return IPS4O_OK;
+        while ((int)st.events.size() < next_event + 2) {
+            cudaEvent_t e;
+            IPS4O_CUDA(cudaEventCreate(&e));
+            st.events.push_back(e);
+        }
+        *slot = next_event;
+        next_event += 2;
+        IPS4O_CUDA(cudaEventRecord(st.events[*slot], stream));
+        timed.push_back(Timed{phase, *slot});
+        return IPS4O_OK;
+    }
+    ips4o_status ev_end(int slot) {
+        st.stats.kernel_launches++;
+        if (slot < 0) return IPS4O_OK;
+        IPS4O_CUDA(cudaEventRecord(st.events[slot + 1], stream));
+        return IPS4O_OK;
+    }
+    ips4o_status collect_events() {
+        for (const Timed& t : timed) {
+            float ms = 0.f;
+            IPS4O_CUDA(cudaEventElapsedTime(&ms, st.events[t.ev], st.events[t.ev + 1]));
+            st.stats.phase_ms[t.phase] += ms;
+            st.stats.phase_launches[t.phase]++;
+        }
+        timed.clear();
+        next_event = 0;
+        return IPS4O_OK;
+    }
+#define IPS4O_LAUNCH(phase, ...)                                  \
+    do {                                                          \
+        int slot_;                                                \
+        ips4o_status rc_ = ev_begin(phase, &slot_);               \
+        if (rc_ != IPS4O_OK) return rc_;                          \
+        __VA_ARGS__;                                              \
+        IPS4O_CUDA(cudaGetLastError());                           \
+        rc_ = ev_end(slot_);                                      \
+        if (rc_ != IPS4O_OK) return rc_;                          \
+    } while (0)
+
+    ips4o_status status_from(u32 bits) {
+        if (bits & kStatusTimeout) return IPS4O_ERR_TIMEOUT;
+        if (bits & (kStatusInternal | kStatusCapacity)) return IPS4O_ERR_INTERNAL;
+        return IPS4O_OK;
+    }
+
+    // Small input: one shared-memory sort.
+    ips4o_status base_only(E* d, u64 n) {
+        h_tasks[0] = Task{0, n};
+        IPS4O_CUDA(cudaMemcpyAsync(ws.next_tasks, h_tasks, sizeof(Task), cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
+        IPS4O_LAUNCH(6, (k_base<T, 512><<<1, 512, T::kBaseCap * sizeof(E), stream>>>(d, ws.next_tasks, 1u, base_cap,
+                                                                                       ws.ctr)));
+        IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
+        IPS4O_CUDA(cudaStreamSynchronize(stream));
+        IPS4O_CUDA(cudaGetLastError());
+        st.stats.base_case_buckets += 1;
+        ips4o_status rc = collect_events();
+        if (rc != IPS4O_OK) return rc;
+        return status_from(h_ctr->status);
+    }
+
+    // Plan one chunk starting at tasks[i0]; returns the number of tasks taken.
+    size_t plan_chunk(const std::vector<Task>& tasks, size_t i0, u64 level_total, u32 level, bool partition,
+                      u32* nsub_out, u32* nstripes_out) {
+        const u64 B = T::kBlock;
+        const u64 target = (u64)std::max(1, prm.stripes_per_sm) * (u64)st.sms;
+        u64 stripe_len = std::max<u64>((level_total + target - 1) / target, kMinStripe);
+        stripe_len = (stripe_len + B - 1) / B * B;
+        u32 nsub = 0, nstr = 0;
+        u64 pool = 0;
+        size_t i = i0;
+        for (; i < tasks.size(); ++i) {
+            const Task t = tasks[i];
+            if (nsub >= caps.max_sub) break;
+            u32 K = partition ? k_max : leaves_for(t.n, base_cap, k_max);
+            u32 alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
+            alpha = std::max<u32>(1, std::min<u32>(alpha, 4096 / K));
+            u64 ns = std::max<u64>(1, (t.n + stripe_len - 1) / stripe_len);
+            ns = std::min<u64>(ns, kMaxStripesPerSub);
+            u64 slen, need;
+            for (;;) {
+                slen = ((t.n + ns - 1) / ns + B - 1) / B * B;
+                ns = (t.n + slen - 1) / slen;
+                need = 0;
+                for (u64 s = 0; s < ns; ++s) {
+                    u64 len = std::min<u64>(slen, t.n - s * slen);
+                    need += std::min<u64>((u64)kMaxBuckets * (B - 1), len);
+                }
+                const bool fits = nstr + ns <= caps.max_stripes && pool + need <= caps.pool_cap;
+                if (fits || ns == 1 || nsub > 0) break;
+                ns = std::max<u64>(1, ns / 2);
+            }
+            if (nstr + ns > caps.max_stripes || pool + need > caps.pool_cap) break;
+            SubDesc& sd = h_subs[nsub];
+            std::memset(&sd, 0, sizeof sd);
+            sd.begin = t.begin;
+            sd.n = t.n;
+            sd.stripe_begin = nstr;
+            sd.num_stripes = (u32)ns;
+            sd.k_target = K;
+            sd.alpha = alpha;
+            sd.level = level;
+            for (u64 s = 0; s < ns; ++s) {
+                StripeDesc& x = h_stripes[nstr + s];
+                x.begin = t.begin + s * slen;
+                x.end = t.begin + std::min<u64>((s + 1) * slen, t.n);
+                x.pool_off = pool;
+                const u64 len = x.end - x.begin;
+                x.pool_cap = (u32)std::min<u64>((u64)kMaxBuckets * (B - 1), len);
+                x.sub = nsub;
+                pool += x.pool_cap;
+            }
+            nstr += (u32)ns;
+            ++nsub;
+        }
+        *nsub_out = nsub;
+        *nstripes_out = nstr;
+        return i - i0;
+    }
+
+    ips4o_status run_chunk(E* d, u32 nsub, u32 nstr, bool partition, u32* next_count) {
+        IPS4O_CUDA(cudaMemcpyAsync(ws.subs, h_subs, nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemcpyAsync(ws.stripes, h_stripes, nstr * sizeof(StripeDesc), cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
+        const u64 seed = prm.seed;
+        IPS4O_LAUNCH(0, (k_sample<T, 512><<<nsub, 512, 0, stream>>>(d, ws, nsub, seed)));
+        const int cgrid = (int)std::min<u32>(nstr, (u32)st.sms);
+        IPS4O_LAUNCH(1, (k_classify<T><<<cgrid, ClassifyCfg<T>::TPB, ClassifyCfg<T>::smem_bytes, stream>>>(d, ws, nstr)));
+        IPS4O_LAUNCH(2, (k_prefix<T, 256><<<nsub, 256, 0, stream>>>(ws, nsub)));
+        IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
+        IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, 0, stream>>>(d, ws, nsub, kSpinLimit)));
+        IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * kMaxBuckets, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                            d, ws, nsub, base_cap, kSpinLimit, partition ? 1u : 0u)));
+        IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
+        IPS4O_CUDA(cudaStreamSynchronize(stream));
+        IPS4O_CUDA(cudaGetLastError());
+        ips4o_status rc = collect_events();
+        if (rc != IPS4O_OK) return rc;
+        st.stats.blocks_moved += h_ctr->blocks_moved;
+        st.stats.blocks_skipped += h_ctr->blocks_skipped;
+        st.stats.fix_blocks_moved += h_ctr->fix_blocks;
+        st.stats.base_case_buckets += h_ctr->base_buckets;
+        st.stats.chunks++;
+        st.stats.subproblems += nsub;
+        rc = status_from(h_ctr->status);
+        if (rc != IPS4O_OK) return rc;
+        *next_count = h_ctr->next_count;
+        return IPS4O_OK;
+    }
+
+    ips4o_status run(E* d, u64 n, PartitionOut* part) {
+        ips4o_status rc = setup(n);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = n;
+        if (!part && n <= base_cap) return base_only(d, n);
+        std::vector<Task> level_tasks{Task{0, n}}, next;
+        u32 level = 0;
+        while (!level_tasks.empty()) {
+            next.clear();
+            u64 level_total = 0;
+            for (const Task& t : level_tasks) level_total += t.n;
+            size_t i = 0;
+            while (i < level_tasks.size()) {
+                u32 nsub = 0, nstr = 0;
+                size_t taken = plan_chunk(level_tasks, i, level_total, level, part != nullptr, &nsub, &nstr);
+                if (taken == 0) return IPS4O_ERR_INTERNAL;
+                u32 cnt = 0;
+                rc = run_chunk(d, nsub, nstr, part != nullptr, &cnt);
+                if (rc != IPS4O_OK) return rc;
+                for (u32 q = 0; q < nsub; ++q) st.stats.elements_distributed += h_subs[q].n;
+                if (cnt > 0) {
+                    if (cnt > caps.next_cap) return IPS4O_ERR_INTERNAL;
+                    IPS4O_CUDA(cudaMemcpyAsync(h_tasks, ws.next_tasks, cnt * sizeof(Task), cudaMemcpyDeviceToHost,
+                                               stream));
+                    IPS4O_CUDA(cudaStreamSynchronize(stream));
+                    next.insert(next.end(), h_tasks, h_tasks + cnt);
+                }
+                i += taken;
+            }
+            ++level;
+            st.stats.levels = level;
+            if (part) {
+                // one distribution step only: export its result
+                SubDesc sd;
+                IPS4O_CUDA(cudaMemcpyAsync(&sd, ws.subs, sizeof(SubDesc), cudaMemcpyDeviceToHost, stream));
+                IPS4O_CUDA(cudaStreamSynchronize(stream));
+                const u32 nb = sd.nbuckets;
+                IPS4O_CUDA(cudaMemcpy(part->bounds, ws.bstart, (nb + 1) * sizeof(u64), cudaMemcpyDeviceToHost));
+                const u32 leaves = 1u << sd.log_leaves;
+                std::vector<K> spl(kMaxLeaves);
+                IPS4O_CUDA(cudaMemcpy(spl.data(), ws.spl, kMaxLeaves * sizeof(K), cudaMemcpyDeviceToHost));
+                for (u32 q = 1; q < leaves; ++q) part->splitters[q - 1] = T::key_bits(spl[q]);
+                *part->num_splitters = leaves - 1;
+                *part->num_buckets = nb;
+                *part->eq = (int)sd.eq;
+                return IPS4O_OK;
+            }
+            level_tasks.swap(next);
+            // guard against a runaway recursion (cannot happen: every level
+            // shrinks every non-equality bucket)
+            if (level > 64) return IPS4O_ERR_INTERNAL;
+        }
+        return IPS4O_OK;
+    }
+};
+
+template <class T>
+ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
+    Driver<T> drv(st, s);
+    return drv.run((typename T::elem_t*)d, (u64)n, part);
+}
+
+}  // namespace ips4o

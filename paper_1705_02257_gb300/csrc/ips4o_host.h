@@ -1,0 +1,50 @@
+// ips4o_host.h — host-side state shared by the per-type drivers and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ips4o.h"
+
+namespace ips4o {
+
+struct DeviceState {
+    int device = -1;
+    int sms = 0;
+    void* d_ws = nullptr;           // workspace (device)
+    size_t ws_bytes = 0;
+    void* h_stage = nullptr;        // pinned host staging for descriptors / readback
+    size_t h_stage_bytes = 0;
+    void* d_host_copy = nullptr;    // device buffer for ips4o_sort_host
+    size_t d_host_copy_bytes = 0;
+    std::vector<cudaEvent_t> events;
+    std::mutex mtx;
+    ips4o_stats stats{};
+};
+
+DeviceState* current_device_state(cudaError_t* err);
+ips4o_params& global_params();
+void set_last_cuda_error(cudaError_t e, const char* where);
+ips4o_status ensure_device_buffer(void** ptr, size_t* have, size_t need);
+ips4o_status ensure_host_pinned(void** ptr, size_t* have, size_t need);
+
+// Per-type entry points (defined in ips4o_<type>.cu).
+struct PartitionOut {
+    uint64_t* bounds;
+    size_t* num_buckets;
+    uint64_t* splitters;
+    size_t* num_splitters;
+    int* eq;
+};
+
+ips4o_status sort_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
+ips4o_status sort_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
+ips4o_status sort_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
+size_t workspace_bytes_u64(size_t n, int sms);
+size_t workspace_bytes_f64(size_t n, int sms);
+size_t workspace_bytes_pair(size_t n, int sms);
+
+}  // namespace ips4o

@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/ips4o.h declares; argument errors are reported before any device
+work (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ips4o.h")
+
+
+def _declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(ips4o_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1705_02257_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared_functions()
+    for expected in ("ips4o_sort", "ips4o_sort_host", "ips4o_partition", "ips4o_workspace_bytes",
+                     "ips4o_get_stats", "ips4o_status_string"):
+        assert expected in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"declared in ips4o.h but not exported: {missing}"
+
+
+def test_argument_errors_without_device_work(lib):
+    from paper_1705_02257_gb300 import ips4o
+    assert ips4o.ips4o_sort(0, 10, ips4o.U64, 0) == 1          # null pointer, n > 0
+    assert ips4o.ips4o_sort(0, 10, 17, 0) == 2                  # unknown key type
+    assert ips4o.ips4o_sort(8 * 1024 + 4, 10, ips4o.U64, 0) == 3  # misaligned
+    assert ips4o.ips4o_sort(0, 0, ips4o.U64, 0) == 0            # empty input: no-op
+    assert ips4o.ips4o_sort(0, 1, ips4o.U64, 0) == 0
+    assert ips4o.ips4o_status_string(6) == "bounded device wait timed out"
+
+
+def test_params_validation(lib):
+    from paper_1705_02257_gb300 import ips4o
+    p = ips4o.ips4o_get_params()
+    assert p.k_max == 256
+    bad = ips4o.Params(100, 0, 0, 2, 0, 1)      # k_max not a power of two
+    assert ips4o.ips4o_set_params(bad) == 1
+    assert ips4o.ips4o_get_params().k_max == 256
+
+
+def test_base_case_capacity(lib):
+    from paper_1705_02257_gb300 import ips4o
+    assert ips4o.ips4o_base_case_capacity(ips4o.U64) == 8192
+    assert ips4o.ips4o_base_case_capacity(ips4o.PAIR_U64) == 4096

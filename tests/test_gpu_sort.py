@@ -1,0 +1,184 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Keys are compared bit for bit with the oracle's output (the sorted key
+sequence is unique).  For pairs the keys are compared bit for bit and the
+(key, payload) multiset is compared exactly, since the method is not stable.
+Sizes cover the shared-memory base case alone, one and two distribution
+levels, n not a multiple of the block size (overflow block), and tiny n.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1705_02257_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ips4o():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1705_02257_gb300 import build
+    build.build()
+    from paper_1705_02257_gb300 import ips4o as m
+    m.reset_params()
+    return m
+
+
+def gpu_sort(ips4o, a, kt):
+    raw = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
+    t = torch.from_numpy(raw.copy()).cuda()
+    ips4o.sort(t, kt)
+    torch.cuda.synchronize()
+    return t.cpu().numpy().view(a.dtype).reshape(a.shape)
+
+
+def check_u64(ips4o, a):
+    got = gpu_sort(ips4o, a, "u64")
+    exp = oracle.sort(a, "u64")
+    if not np.array_equal(got, exp):
+        bad = np.nonzero(got != exp)[0]
+        raise AssertionError(f"{len(bad)} mismatches, first at {bad[:5]} (n={len(a)})")
+
+
+EDGE_SIZES = [0, 1, 2, 3, 31, 63, 64, 65, 1000, 8191, 8192, 8193, 8256, 16385, 100003]
+
+
+@pytest.mark.parametrize("n", EDGE_SIZES)
+@pytest.mark.parametrize("dist", ["uniform", "ones", "two_dup", "sorted"])
+def test_u64_edge_sizes(ips4o, n, dist):
+    check_u64(ips4o, inputs.u64(n, dist))
+
+
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+def test_u64_all_distributions_2pow20(ips4o, dist):
+    check_u64(ips4o, inputs.u64(1 << 20, dist))
+
+
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+def test_u64_all_distributions_ragged_two_levels(ips4o, dist):
+    # 3,000,017 keys: several stripes, two distribution levels, n % b != 0
+    check_u64(ips4o, inputs.u64(3_000_017, dist))
+
+
+def test_u64_repeated_calls_same_result(ips4o):
+    a = inputs.u64(500_001, "exponential")
+    r1 = gpu_sort(ips4o, a, "u64")
+    r2 = gpu_sort(ips4o, a, "u64")
+    assert np.array_equal(r1, r2)
+    assert np.array_equal(r1, oracle.sort(a, "u64"))
+
+
+@pytest.mark.parametrize("n", [5, 8193, 1 << 20, 1_234_567])
+def test_f64(ips4o, n):
+    a = inputs.f64(n)
+    got = gpu_sort(ips4o, a, "f64")
+    assert np.array_equal(got.view(np.uint64), oracle.sort(a, "f64").view(np.uint64))
+
+
+def test_f64_negative_and_special_values(ips4o):
+    rng = np.random.default_rng(11)
+    a = np.concatenate([rng.standard_normal(300_000) * 1e3,
+                        np.array([0.0, -0.0, np.inf, -np.inf, 5e-324, -5e-324] * 1000)])
+    rng.shuffle(a)
+    got = gpu_sort(ips4o, a, "f64")
+    assert np.array_equal(got.view(np.uint64), oracle.sort(a, "f64").view(np.uint64))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "root_dup", "ones", "eight_dup"])
+@pytest.mark.parametrize("n", [4097, 700_001])
+def test_pair(ips4o, dist, n):
+    p = inputs.pair(n, dist)
+    got = gpu_sort(ips4o, p, "pair")
+    exp = oracle.sort(p, "pair")
+    assert np.array_equal(got["key"], exp["key"])
+    assert np.array_equal(np.sort(got, order=["key", "payload"]), np.sort(p, order=["key", "payload"]))
+
+
+def _mapped_keys(a, kt):
+    if kt == "u64":
+        return a.view(np.uint64)
+    if kt == "f64":
+        b = a.view(np.uint64)
+        return np.where(b >> np.uint64(63) == 1, ~b, b | np.uint64(1 << 63))
+    if kt == "pair":
+        return a["key"]
+    raise ValueError(kt)
+
+
+@pytest.mark.parametrize("kt,dist,n", [
+    ("u64", "uniform", 1 << 20), ("u64", "root_dup", 1 << 20), ("u64", "ones", 300_000),
+    ("u64", "exponential", 2_000_003), ("u64", "two_dup", 1 << 20), ("f64", "uniform", 777_777),
+    ("pair", "root_dup", 500_000), ("u64", "uniform", 100), ("u64", "uniform", 7),
+])
+def test_partition_bucket_rule(ips4o, kt, dist, n):
+    """One distribution step: every bucket holds exactly the keys the
+    splitters assign to it (Section 3, s_i <= e < s_{i+1}; Section 4.4,
+    equality buckets hold one key), and the step permutes the input."""
+    a = inputs.make(kt, n, dist)
+    raw = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
+    t = torch.from_numpy(raw.copy()).cuda()
+    bounds, spl, eq = ips4o.partition(t, kt)
+    torch.cuda.synchronize()
+    out = t.cpu().numpy().view(a.dtype).reshape(a.shape)
+    assert bounds[0] == 0 and bounds[-1] == n and np.all(np.diff(bounds) >= 0)
+    assert np.all(spl[1:] >= spl[:-1])
+    keys = _mapped_keys(out, kt)
+    nb = len(bounds) - 1
+    assert nb == (2 * (len(spl) + 1) - 1 if eq else len(spl) + 1)
+    for b in range(nb):
+        seg = keys[bounds[b]:bounds[b + 1]]
+        if len(seg) == 0:
+            continue
+        if eq:
+            i = b // 2
+            if b % 2 == 1:
+                assert np.all(seg == spl[i]), f"equality bucket {b}"
+                continue
+            if i >= 1:
+                assert np.all(seg > spl[i - 1]), f"bucket {b} lower bound"
+            if i < len(spl):
+                assert np.all(seg < spl[i]), f"bucket {b} upper bound"
+        else:
+            if b >= 1:
+                assert np.all(seg >= spl[b - 1]), f"bucket {b} lower bound"
+            if b < len(spl):
+                assert np.all(seg < spl[b]), f"bucket {b} upper bound"
+    # a permutation of the input
+    assert oracle.multiset_hash(out, kt) == oracle.multiset_hash(a, kt)
+
+
+def test_ones_single_equality_bucket(ips4o):
+    a = inputs.u64(200_000, "ones")
+    t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    bounds, spl, eq = ips4o.partition(t, "u64")
+    sizes = np.diff(bounds)
+    assert eq
+    assert sizes.max() == len(a)
+    big = int(np.argmax(sizes))
+    assert big % 2 == 1 and spl[big // 2] == 1
+
+
+def test_stats_counters(ips4o):
+    a = inputs.u64(1 << 22)
+    t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    ips4o.sort(t, "u64")
+    torch.cuda.synchronize()
+    st = ips4o.stats()
+    assert st["n"] == 1 << 22
+    assert st["levels"] >= 1
+    assert st["blocks_moved"] > 0
+    assert st["base_case_buckets"] > 0
+    assert st["workspace_bytes"] > 0
+    # Theorem 2: the extra space is O(k b t + #subproblems), far below n
+    assert st["workspace_bytes"] < 8 * (1 << 22)
+
+
+def test_sort_host_roundtrip(ips4o):
+    a = inputs.u64(1_000_003, "two_dup")
+    b = a.copy()
+    ips4o.sort_host(b, "u64")
+    assert np.array_equal(b, oracle.sort(a, "u64"))
