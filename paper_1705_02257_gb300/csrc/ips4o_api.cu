@@ -22,6 +22,8 @@ thread_local char g_last_err[256] = {0};
 
 ips4o_params& global_params() { return g_params; }
 
+void set_last_message(const char* msg) { std::snprintf(g_last_err, sizeof g_last_err, "%s", msg); }
+
 void set_last_cuda_error(cudaError_t e, const char* where) {
     std::snprintf(g_last_err, sizeof g_last_err, "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
 }

@@ -112,7 +112,10 @@ struct ChunkCounters {
     u32 ticket;         // cleanup ticket dispenser
     u32 next_count;     // tasks emitted for the next level
     u32 status;         // error bits
-    u32 pad[3];
+    u32 guard_line;     // first failed bounds guard: source line (0 = none)
+    u32 guard_hits;     // number of failed bounds guards
+    u32 pad;
+    u64 guard_a, guard_b;   // operands of the first failed guard
     u64 blocks_moved;
     u64 blocks_skipped;
     u64 fix_blocks;
@@ -133,6 +136,7 @@ struct Workspace {
     u64* wr;                  // [max_sub][256]   packed (w_i << 32) | (r_i + bias)
     u32* readers;             // [max_sub][256]   threads currently reading from bucket i
     u32* flags;               // [max_sub][256]   cleanup hand-over flags
+    u32* exhausted;           // [max_sub][8]     bitmap of buckets without unprocessed blocks
     u32* region_full;         // [max_sub][256]   full blocks inside region [d_i, d_{i+1})
     u32* bucket_full;         // [max_sub][256]   full blocks of bucket i (all stripes)
     u32* counts;              // [max_stripes][256] elements per bucket per stripe
@@ -184,6 +188,14 @@ __device__ __forceinline__ u32 ld_acquire(const u32* p) {
 __device__ __forceinline__ void st_release(u32* p, u32 v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+__device__ __forceinline__ void red_add_release(u32* p, u32 v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ u32 ld_relaxed(const u32* p) {
+    u32 v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void red_add_relaxed(u32* p, u32 v) {
     asm volatile("red.relaxed.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -197,6 +209,18 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 __host__ __device__ __forceinline__ u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ void set_status(ChunkCounters* c, u32 bits) { atomicOr(&c->status, bits); }
+
+// A failed bounds guard: the access is skipped, the chunk reports an
+// internal error, and the first failure's line and operands are kept.
+static __device__ __noinline__ void guard_fail(ChunkCounters* c, u32 line, u64 a, u64 b) {
+    if (atomicAdd(&c->guard_hits, 1u) == 0) {
+        c->guard_line = line;
+        c->guard_a = a;
+        c->guard_b = b;
+    }
+    atomicOr(&c->status, kStatusInternal);
+}
+#define IPS4O_GUARD(ctr, cond, a, b) ((cond) ? true : (guard_fail((ctr), __LINE__, (u64)(a), (u64)(b)), false))
 
 // Bucket of key e (Section 3): descend the implicit tree a[1..L-1]
 // (a_1 = s_{L/2}, children of a_j are a_{2j}, a_{2j+1}) with j = 2j + (a_j <= e);

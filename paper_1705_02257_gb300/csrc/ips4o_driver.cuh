@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 #include "ips4o_host.h"
@@ -74,6 +75,7 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.wr = (u64*)take(S * kMaxBuckets * 8);
     w.readers = (u32*)take(S * kMaxBuckets * 4);
     w.flags = (u32*)take(S * kMaxBuckets * 4);
+    w.exhausted = (u32*)take(S * 8 * 4);
     w.region_full = (u32*)take(S * kMaxBuckets * 4);
     w.bucket_full = (u32*)take(S * kMaxBuckets * 4);
     w.counts = (u32*)take(R * kMaxBuckets * 4);
@@ -106,14 +108,18 @@ size_t workspace_bytes_t(size_t n, int sms) {
     return carve<T>(c, nullptr, nullptr);
 }
 
-// Number of leaves for a subproblem of n elements (Section 4.7, adaptive k
-// on the last two levels): the reduction 2n/T to reach half the base-case
-// capacity T is taken in one step when k_max allows, split evenly over two
-// steps when k_max^2 allows, and k_max is used otherwise.
+// Number of leaves for a subproblem of n elements (Section 4.7, adaptive
+// number of buckets on the last levels).  r = 2n/T is the reduction that
+// brings the average bucket to half the base-case capacity T.  One step
+// with pow2(r) leaves when r <= k_max; still one step with k_max leaves when
+// r <= 2*k_max (average bucket <= T; the few larger buckets take one more
+// step); two balanced steps of about sqrt(r) leaves when r <= k_max^2; and
+// k_max otherwise.
 inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
     const double r = 2.0 * (double)n / (double)base_cap;
     u32 k;
     if (r <= (double)k_max) k = pow2_ceil_host((u64)std::ceil(r));
+    else if (r <= 2.0 * (double)k_max) k = k_max;
     else if (r <= (double)k_max * (double)k_max) k = pow2_ceil_host((u64)std::ceil(std::sqrt(r)));
     else k = k_max;
     return std::min(std::max<u32>(k, 4), k_max);
@@ -176,8 +182,8 @@ struct Driver {
                                         (int)ClassifyCfg<T>::smem_bytes));
         IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)CleanupCfg<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, 512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)(T::kBaseCap * sizeof(E))));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)BaseCfg<T>::smem_bytes));
         int occ = 0;
         IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB, 0));
         permute_grid = std::max(1, occ) * st.sms;
@@ -230,6 +236,13 @@ struct Driver {
     } while (0)
 
     ips4o_status status_from(u32 bits) {
+        if (h_ctr->guard_hits) {
+            char msg[160];
+            std::snprintf(msg, sizeof msg, "device bounds guard failed %u time(s); first at kernels line %u (%llu, %llu)",
+                          h_ctr->guard_hits, h_ctr->guard_line, (unsigned long long)h_ctr->guard_a,
+                          (unsigned long long)h_ctr->guard_b);
+            set_last_message(msg);
+        }
         if (bits & kStatusTimeout) return IPS4O_ERR_TIMEOUT;
         if (bits & (kStatusInternal | kStatusCapacity)) return IPS4O_ERR_INTERNAL;
         return IPS4O_OK;
@@ -240,8 +253,8 @@ struct Driver {
         h_tasks[0] = Task{0, n};
         IPS4O_CUDA(cudaMemcpyAsync(ws.next_tasks, h_tasks, sizeof(Task), cudaMemcpyHostToDevice, stream));
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
-        IPS4O_LAUNCH(6, (k_base<T, 512><<<1, 512, T::kBaseCap * sizeof(E), stream>>>(d, ws.next_tasks, 1u, base_cap,
-                                                                                       ws.ctr)));
+        IPS4O_LAUNCH(6, (k_base<T><<<1, BaseCfg<T>::TPB, BaseCfg<T>::smem_bytes, stream>>>(d, ws.next_tasks, 1u, ws.ctr,
+                                                                                             prm.seed)));
         IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
         IPS4O_CUDA(cudaStreamSynchronize(stream));
         IPS4O_CUDA(cudaGetLastError());
@@ -322,7 +335,7 @@ struct Driver {
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, 0, stream>>>(d, ws, nsub, kSpinLimit)));
         IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * kMaxBuckets, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nsub, base_cap, kSpinLimit, partition ? 1u : 0u)));
+                            d, ws, nsub, base_cap, kSpinLimit, partition ? 1u : 0u, seed)));
         IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
         IPS4O_CUDA(cudaStreamSynchronize(stream));
         IPS4O_CUDA(cudaGetLastError());

@@ -28,6 +28,7 @@ struct DeviceState {
 DeviceState* current_device_state(cudaError_t* err);
 ips4o_params& global_params();
 void set_last_cuda_error(cudaError_t e, const char* where);
+void set_last_message(const char* msg);
 ips4o_status ensure_device_buffer(void** ptr, size_t* have, size_t need);
 ips4o_status ensure_host_pinned(void** ptr, size_t* have, size_t need);
 

@@ -29,79 +29,10 @@
 //   k_base       Section 4.7 base case for whole small inputs / segments.
 #pragma once
 
+#include "ips4o_basecase.cuh"
 #include "ips4o_common.cuh"
 
 namespace ips4o {
-
-template <class K>
-__device__ __forceinline__ K key_max();
-template <>
-__device__ __forceinline__ u64 key_max<u64>() { return ~0ull; }
-
-__device__ __forceinline__ u32 pow2_ceil_u32(u32 x) {
-    return x <= 1 ? 1u : (1u << (32 - __clz(x - 1)));
-}
-
-// ------------------------------------------------------------ base case
-// In-place sort of s[0..n) in shared memory: a bitonic network whose merge
-// stages start by comparing element i with its mirror (i ^ (size-1)), so
-// every comparator puts the smaller key at the lower index and the
-// positions >= n behave as +infinity and are never touched.
-template <class T, int TPB>
-__device__ void smem_sort(typename T::elem_t* s, u32 n) {
-    typedef typename T::elem_t E;
-    if (n < 2) return;
-    const u32 P = pow2_ceil_u32(n);
-    for (u32 k = 2; k <= P; k <<= 1) {
-        const u32 half = k >> 1;
-        for (u32 t = threadIdx.x; t < P / 2; t += TPB) {
-            u32 i = (t / half) * k + (t % half);
-            u32 j = i ^ (k - 1);
-            if (j < n) {
-                E a = s[i], b = s[j];
-                if (T::key(b) < T::key(a)) { s[i] = b; s[j] = a; }
-            }
-        }
-        __syncthreads();
-        for (u32 st = k >> 2; st > 0; st >>= 1) {
-            for (u32 t = threadIdx.x; t < P / 2; t += TPB) {
-                u32 i = (t / st) * 2 * st + (t % st);
-                u32 j = i + st;
-                if (j < n) {
-                    E a = s[i], b = s[j];
-                    if (T::key(b) < T::key(a)) { s[i] = b; s[j] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
-template <class T, int TPB>
-__device__ void sort_range_in_smem(typename T::elem_t* A, u64 n, typename T::elem_t* sbuf) {
-    for (u32 i = threadIdx.x; i < n; i += TPB) sbuf[i] = A[i];
-    __syncthreads();
-    smem_sort<T, TPB>(sbuf, (u32)n);
-    for (u32 i = threadIdx.x; i < n; i += TPB) A[i] = sbuf[i];
-    __syncthreads();
-}
-
-// Whole segments of at most `cap` elements: one CTA per segment.
-// seg_begin/seg_n describe segment i (absolute offsets).
-template <class T, int TPB>
-__global__ void __launch_bounds__(TPB) k_base(typename T::elem_t* arr, const Task* segs, u32 nseg, u32 cap,
-                                              ChunkCounters* ctr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    typename T::elem_t* sbuf = (typename T::elem_t*)smem_raw;
-    for (u32 i = blockIdx.x; i < nseg; i += gridDim.x) {
-        Task t = segs[i];
-        if (t.n > cap) {
-            if (threadIdx.x == 0) set_status(ctr, kStatusInternal);
-            continue;
-        }
-        sort_range_in_smem<T, TPB>(arr + t.begin, t.n, sbuf);
-    }
-}
 
 // ------------------------------------------------------------- sampling
 template <class T, int TPB>
@@ -128,61 +59,12 @@ __global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, W
         }
     }
     __syncthreads();
-    // bitonic sort of the (power-of-two padded) sample
-    for (u32 k = 2; k <= P; k <<= 1) {
-        for (u32 jj = k >> 1; jj > 0; jj >>= 1) {
-            for (u32 i = threadIdx.x; i < P; i += TPB) {
-                u32 ixj = i ^ jj;
-                if (ixj > i) {
-                    K a = keys[i], b = keys[ixj];
-                    bool up = (i & k) == 0;
-                    if ((a > b) == up) { keys[i] = b; keys[ixj] = a; }
-                }
-            }
-            __syncthreads();
-        }
-    }
-    // k-1 equally spaced splitters s_j = sample[j*alpha - 1]
-    u32 ncand = kk - 1;
-    if (threadIdx.x < ncand) cand[threadIdx.x] = keys[(threadIdx.x + 1) * alpha - 1];
-    __syncthreads();
-    int dup = (threadIdx.x > 0 && threadIdx.x < ncand && cand[threadIdx.x] == cand[threadIdx.x - 1]) ? 1 : 0;
-    const bool eq = __syncthreads_or(dup) != 0;
-    if (eq && kk >= 4) {
-        // Equality buckets double the bucket count; keep it within 256 by
-        // reselecting with k/2 splitters (spacing 2*alpha).
-        ncand = kk / 2 - 1;
-        if (threadIdx.x < ncand) cand[threadIdx.x] = keys[(threadIdx.x + 1) * 2 * alpha - 1];
-        __syncthreads();
-    }
-    // remove duplicates (stable compaction)
-    u32 keep = (threadIdx.x < ncand && (threadIdx.x == 0 || cand[threadIdx.x] != cand[threadIdx.x - 1])) ? 1u : 0u;
-    K mine = threadIdx.x < ncand ? cand[threadIdx.x] : K(0);
-    u32 m;
-    u32 pos = block_exclusive_scan<u32>(keep, scan_tmp, &m);
-    __syncthreads();
-    if (keep) cand[pos] = mine;
-    __syncthreads();
-    if (m == 0) m = 1;   // cannot happen (ncand >= 1), kept for safety
-    const u32 L = pow2_ceil_u32(m + 1);
-    u32 logL = 31 - __clz(L);
-    K* spl = ws.spl + (u64)j * kMaxLeaves;
-    K* tree = ws.tree + (u64)j * kMaxLeaves;
-    // padded sorted splitters s_1..s_{L-1} (s_i = s_m for i > m)
-    for (u32 i = threadIdx.x; i < kMaxLeaves; i += TPB) {
-        K v = cand[(i >= 1 ? (i <= m ? i : m) : 1) - 1];
-        spl[i] = v;
-    }
-    // implicit tree: node v at depth dd holds s_{(2*(v - 2^dd) + 1) * L / 2^(dd+1)}
-    for (u32 v = threadIdx.x; v < kMaxLeaves; v += TPB) {
-        K val = cand[0];
-        if (v >= 1 && v < L) {
-            u32 dd = 31 - __clz(v);
-            u32 idx = (2 * (v - (1u << dd)) + 1) * (L >> (dd + 1));
-            val = cand[(idx <= m ? idx : m) - 1];
-        }
-        tree[v] = val;
-    }
+    sort_sample<K, TPB>(keys, P);
+    u32 logL;
+    bool eq;
+    select_splitters<K>(keys, kk, alpha, cand, scan_tmp, ws.tree + (u64)j * kMaxLeaves, ws.spl + (u64)j * kMaxLeaves,
+                        &logL, &eq);
+    const u32 L = 1u << logL;
     if (threadIdx.x == 0) {
         ws.subs[j].log_leaves = logL;
         ws.subs[j].eq = eq ? 1u : 0u;
@@ -195,13 +77,13 @@ template <class T>
 struct ClassifyCfg {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    static constexpr int TPB = 512;
+    static constexpr int TPB = 1024;
     static constexpr int NW = TPB / 32;
-    static constexpr int STAGES = 3;
-    static constexpr int TILE = 16384 / (int)sizeof(E);        // 16 KiB per tile
+    static constexpr int STAGES = 2;
+    static constexpr int TILE = 32768 / (int)sizeof(E);        // 32 KiB per tile
     static constexpr int IPT = TILE / TPB;
     static constexpr int B = T::kBlock;
-    static constexpr int MAXBLK = 320;                        // >= (256*(B-1) + TILE) / B
+    static constexpr int MAXBLK = 352;                        // >= (256*(B-1) + TILE) / B
     static constexpr size_t off_buf = 0;
     static constexpr size_t off_stage = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
     static constexpr size_t off_tree = off_stage + (size_t)STAGES * TILE * sizeof(E);
@@ -217,6 +99,29 @@ struct ClassifyCfg {
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
     static_assert(TILE % TPB == 0, "tile must be a multiple of the CTA size");
 };
+
+// Bucket ids of IPT keys, descending the tree level by level for all keys at
+// once so that the IPT independent shared-memory lookups overlap.
+template <class K, int IPT>
+__device__ __forceinline__ void classify_many(const K (&k)[IPT], const bool (&valid)[IPT], const K* tree,
+                                              const K* spl, int logL, bool eq, int (&bk)[IPT]) {
+    int j[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) j[q] = 1;
+#pragma unroll
+    for (int l = 0; l < 8; ++l) {
+        if (l < logL) {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) j[q] = 2 * j[q] + (tree[j[q]] <= k[q] ? 1 : 0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        int i = j[q] - (1 << logL);
+        if (eq) i = 2 * i - ((i > 0 && spl[i] == k[q]) ? 1 : 0);
+        bk[q] = valid[q] ? i : -1;
+    }
+}
 
 template <class T>
 __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
@@ -282,23 +187,30 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
             const u64 tb = (u64)t * TILE;
             const u32 tcount = (u32)((len - tb) < (u64)TILE ? (len - tb) : (u64)TILE);
             E e[IPT];
+            K k[IPT];
+            bool valid[IPT];
             int bk[IPT];
             u32 rk[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
-                u32 idx = tid + q * TPB;
-                bk[q] = -1;
-                if (idx < tcount) {
-                    e[q] = tile[idx];
-                    bk[q] = classify_key<K>(T::key(e[q]), s_tree, s_spl, logL, eq);
+                const u32 idx = tid + q * TPB;
+                valid[q] = idx < tcount;
+                e[q] = tile[valid[q] ? idx : 0];
+                k[q] = T::key(e[q]);
+            }
+            classify_many<K, IPT>(k, valid, s_tree, s_spl, logL, eq, bk);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                // rank within the tile's run of the bucket; a warp whose lanes
+                // all hit one bucket (long runs, repeated keys) takes one atomic
+                const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
+                if (__all_sync(0xffffffffu, bk[q] == b0)) {
+                    u32 base = 0;
+                    if (lane == 0 && b0 >= 0) base = atomicAdd(&s_cnt[b0], 32u);
+                    rk[q] = __shfl_sync(0xffffffffu, base, 0) + lane;
+                } else {
+                    rk[q] = bk[q] >= 0 ? atomicAdd(&s_cnt[bk[q]], 1u) : 0u;
                 }
-                // rank within the tile's run of the bucket, aggregated per warp
-                unsigned peers = __match_any_sync(0xffffffffu, bk[q]);
-                int leader = __ffs(peers) - 1;
-                u32 base = 0;
-                if (lane == leader && bk[q] >= 0) base = atomicAdd(&s_cnt[bk[q]], (u32)__popc(peers));
-                base = __shfl_sync(0xffffffffu, base, leader);
-                rk[q] = base + __popc(peers & ((1u << lane) - 1u));
             }
             __syncthreads();
             // per-bucket run offsets in the tile and full blocks to emit
@@ -309,7 +221,7 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
                 nfull = (f + c) / B;
             }
             u64 tot;
-            u64 pre = block_exclusive_scan<u64>(((u64)c << 32) | nfull, s_misc, &tot);
+            const u64 pre = block_exclusive_scan<u64>(((u64)c << 32) | nfull, s_misc, &tot);
             const u32 tot_blocks = (u32)(tot & 0xffffffffu);
             if (tid < kMaxBuckets) {
                 s_off[tid] = (u32)(pre >> 32);
@@ -457,6 +369,13 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
         }
     }
     if (b == 0) delim[nb] = s_delim[nb];
+    if (b < 8) {
+        // buckets beyond nb never hold blocks: mark them exhausted
+        u32 word = 0;
+        for (int q = 0; q < 32; ++q)
+            if ((u32)(b * 32 + q) >= nb) word |= 1u << q;
+        ws.exhausted[(u64)j * 8 + b] = word;
+    }
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < ns; ++i) blocks += s_full[i];
         ws.subs[j].blocks_total = blocks;
@@ -544,20 +463,29 @@ __global__ void __launch_bounds__(TPB) k_fix(typename T::elem_t* arr, Workspace<
 }
 
 // --------------------------------------------------- block permutation
+//
+// A mover is the GPU counterpart of one thread of Section 4.2: it owns a
+// primary bucket, takes unprocessed blocks from it by decrementing r_p, and
+// carries each block to its destination bucket t by incrementing w_t: a swap
+// with the unprocessed block found there (or a skip when that block already
+// belongs to t), or a write into an empty slot, after which it reads again.
+// (w_i, r_i) live in one 64-bit word updated with single atomic adds, so
+// every mover sees both pointers consistently.  A reader count per bucket
+// protects a block that has been claimed but not yet read: writes into
+// empty slots wait (boundedly) until no mover is reading from the bucket.
+//
+// Each warp runs V movers in lockstep: their pointer atomics, block loads
+// and block stores are issued by the same instructions, so one warp keeps
+// V blocks in flight.
 template <class T>
 struct PermuteCfg {
     static constexpr int TPB = 256;
     static constexpr int NW = TPB / 32;
+    static constexpr int V = 4;                  // movers per warp
     static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block
+    static constexpr int MAX_MOVERS_PER_BUCKET = 64;
     static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
 };
-
-template <class T>
-__device__ __forceinline__ int classify_block_head(const typename T::elem_t* blk, const typename T::key_t* tree,
-                                                   const typename T::key_t* spl, int logL, bool eq,
-                                                   typename T::elem_t first) {
-    return classify_key<typename T::key_t>(T::key(first), tree, spl, logL, eq);
-}
 
 template <class T>
 __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
@@ -565,13 +493,13 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
-    constexpr int TPB = C::TPB, NW = C::NW, EPL = C::EPL, B = T::kBlock;
-    __shared__ u32 s_mpre[1025];
+    constexpr int TPB = C::TPB, NW = C::NW, V = C::V, EPL = C::EPL, B = T::kBlock;
+    __shared__ u32 s_gpre[1025];
     __shared__ u64 s_tot;
     __shared__ u32 tmp[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const u32 M = gridDim.x * NW;
-    // movers per subproblem in proportion to its full blocks (at least one)
+    const u32 G = gridDim.x * NW;                 // warps in the grid
+    // mover groups (warps) per subproblem, in proportion to its full blocks
     u64 mine = 0;
     for (u32 i = threadIdx.x; i < nsub; i += TPB) mine += ws.subs[i].blocks_total;
     if (threadIdx.x == 0) s_tot = 0;
@@ -580,42 +508,46 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
     __syncthreads();
     const u64 total = s_tot;
     {
-        // scan over nsub (<= 1024) entries, PER per thread
         constexpr int PER = 1024 / TPB;
-        u32 mv[PER], sum = 0;
+        u32 gv[PER], sum = 0;
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const u32 i = threadIdx.x * PER + q;
-            mv[q] = 0;
+            gv[q] = 0;
             if (i < nsub && total > 0) {
-                const u64 bl = ws.subs[i].blocks_total;
+                const SubDesc& sd = ws.subs[i];
+                const u64 bl = sd.blocks_total;
                 if (bl > 0) {
-                    u64 x = bl * (u64)M / total;
-                    mv[q] = (u32)(x < 1 ? 1 : (x > 0x10000000ull ? 0x10000000ull : x));
+                    u64 x = (bl * (u64)G + total - 1) / total;
+                    const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + V - 1) / V;
+                    const u64 cap_k = (bl + V - 1) / V;
+                    x = x < cap_b ? x : cap_b;
+                    x = x < cap_k ? x : cap_k;
+                    gv[q] = (u32)(x < 1 ? 1 : x);
                 }
             }
-            sum += mv[q];
+            sum += gv[q];
         }
         u32 tot;
         u32 p = block_exclusive_scan<u32>(sum, tmp, &tot);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const u32 i = threadIdx.x * PER + q;
-            if (i < nsub) s_mpre[i] = p;
-            p += mv[q];
+            if (i < nsub) s_gpre[i] = p;
+            p += gv[q];
         }
-        if (threadIdx.x == 0) s_mpre[nsub] = tot;
+        if (threadIdx.x == 0) s_gpre[nsub] = tot;
         __syncthreads();
     }
-    const u32 V = s_mpre[nsub];
+    const u32 GT = s_gpre[nsub];
     u64 moved = 0, skipped = 0;
     bool failed = false;
-    for (u32 v = blockIdx.x * NW + warp; v < V && !failed; v += M) {
+    for (u32 g = blockIdx.x * NW + warp; g < GT && !failed; g += G) {
         u32 lo = 0, hi = nsub;
-        while (hi - lo > 1) { u32 mid = (lo + hi) >> 1; if (s_mpre[mid] <= v) lo = mid; else hi = mid; }
+        while (hi - lo > 1) { u32 mid = (lo + hi) >> 1; if (s_gpre[mid] <= g) lo = mid; else hi = mid; }
         const u32 j = lo;
-        const u32 local = v - s_mpre[j];
-        const u32 nmov = s_mpre[j + 1] - s_mpre[j];
+        const u32 gl = g - s_gpre[j];
+        const u32 nmov = (s_gpre[j + 1] - s_gpre[j]) * V;
         const SubDesc sub = ws.subs[j];
         const u32 nb = sub.nbuckets;
         const int logL = (int)sub.log_leaves;
@@ -629,93 +561,228 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
         E* ovf = ws.overflow + (u64)j * B;
         const u64 nbc = sub.n / B;                   // complete block slots
         const bool partial = (sub.n % B) != 0;
-        const u32 p0 = (u32)(((u64)local * nb) / (nmov ? nmov : 1));
-        E buf[EPL], tmpb[EPL];
-        for (u32 step = 0; step < nb && !failed; ++step) {
-            const u32 p = (p0 + step) % nb;
-            for (;;) {
-                // take an unprocessed block from the primary bucket: r_p--
-                u64 old = 0;
-                if (lane == 0) {
-                    red_add_relaxed(&readers[p], 1u);
-                    old = atom_add_acq_rel(&wr[p], ~0ull);
+
+        u32* exh = ws.exhausted + (u64)j * 8;
+        // per-mover state (arrays indexed by compile-time v only)
+        E buf[V][EPL], tmpb[V][EPL];
+        u32 prim[V], tgt[V];
+        bool have[V], done[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            prim[v] = (u32)(((u64)(gl * V + v) * nb) / nmov);
+            tgt[v] = 0;
+            have[v] = false;
+            done[v] = false;
+        }
+        // lanes 0..7 hold one word each of the exhausted-bucket bitmap
+        u32 exw = lane < 8 ? ld_relaxed(&exh[lane]) : 0xffffffffu;
+        for (;;) {
+            bool any_active = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) any_active |= !done[v];
+            if (!any_active || failed) break;
+            // ---- movers with empty hands pick a primary bucket that still has
+            // unprocessed blocks (next one cyclically, as in Section 4.2)
+            bool want = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) want |= (!have[v] && !done[v]);
+            if (want) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (have[v] || done[v]) continue;
+                    // first non-exhausted bucket at or after prim (cyclic)
+                    const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
+                    // word index w relative to pw: lane l looks at word (pw + l) % 8 masked
+                    const u32 wi = (pw + (u32)lane) & 7u;
+                    const u32 word_l = __shfl_sync(0xffffffffu, exw, wi);     // all lanes shuffle
+                    const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
+                    u32 free_bits = 0u;
+                    if (lane < 8) free_bits = ~word_l;
+                    if (lane == 0) free_bits &= ~((1u << pb) - 1u);      // at or after prim in its word
+                    // wrap-around: bits before prim in word pw are checked last (lane 8)
+                    if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
+                    const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
+                    if (ball == 0) {
+                        done[v] = true;
+                        continue;
+                    }
+                    const int first = __ffs(ball) - 1;
+                    const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
+                    const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
+                    const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
+                    if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
+                    else { failed = true; done[v] = true; }
                 }
-                old = __shfl_sync(0xffffffffu, old, 0);
-                const long long w = (long long)(old >> 32);
-                const long long r = (long long)(u32)(old & 0xffffffffull) - (long long)kPtrBias;
-                if (r < w) {
-                    if (lane == 0) red_add_relaxed(&readers[p], ~0u);
-                    break;                                   // bucket p has no unprocessed blocks left
+            }
+            // ---- take a block from the primary bucket: r_p--
+            u64 aold = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (lane == v && !have[v] && !done[v]) {
+                    red_add_relaxed(&readers[prim[v]], 1u);
+                    aold = atom_add_acq_rel(&wr[prim[v]], ~0ull);
                 }
-                if (r < 0 || (u64)(r + 1) * B > sub.n) {
-                    if (lane == 0) { set_status(ws.ctr, kStatusInternal); red_add_relaxed(&readers[p], ~0u); }
+            bool got[V];
+            u64 rslot[V];
+            bool any_got = false, any_exh = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const u64 o = __shfl_sync(0xffffffffu, aold, v);
+                got[v] = false;
+                rslot[v] = 0;
+                if (!have[v] && !done[v]) {
+                    const long long w = (long long)(o >> 32);
+                    const long long r = (long long)(u32)(o & 0xffffffffull) - (long long)kPtrBias;
+                    if (r < w) {
+                        if (lane == v) {
+                            red_add_relaxed(&readers[prim[v]], ~0u);
+                            atomicOr(&exh[prim[v] >> 5], 1u << (prim[v] & 31));
+                        }
+                        any_exh = true;
+                    } else if (!IPS4O_GUARD(ws.ctr, r >= 0 && (u64)(r + 1) * B <= nbc * B, r, nbc)) {
+                        if (lane == v) red_add_relaxed(&readers[prim[v]], ~0u);
+                        failed = true;
+                    } else {
+                        got[v] = true;
+                        rslot[v] = (u64)r;
+                        any_got = true;
+                    }
+                }
+            }
+            if (failed) {
+                if (lane == 0) set_status(ws.ctr, kStatusInternal);
+                break;
+            }
+            if (any_exh) {
+                __syncwarp();
+                if (lane < 8) exw = ld_relaxed(&exh[lane]);
+            }
+            if (any_got) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (got[v]) {
+#pragma unroll
+                        for (int q = 0; q < EPL; ++q) buf[v][q] = A[rslot[v] * B + lane + 32 * q];
+                    }
+                int mybk = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const K hk = __shfl_sync(0xffffffffu, T::key(buf[v][0]), 0);
+                    if (lane == v && got[v]) mybk = classify_key<K>(hk, tree, spl, logL, eq);
+                }
+                // the warp barrier orders every lane's block loads before the
+                // release decrement of the reader count (release is cumulative),
+                // so a writer that sees the count drop cannot overwrite a slot
+                // still being read
+                __syncwarp();
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (lane == v && got[v]) red_add_release(&readers[prim[v]], ~0u);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const int t = __shfl_sync(0xffffffffu, mybk, v);
+                    if (got[v]) {
+                        if (IPS4O_GUARD(ws.ctr, t >= 0 && (u32)t < nb, t, nb)) { have[v] = true; tgt[v] = (u32)t; }
+                        else failed = true;
+                    }
+                }
+            }
+            // ---- carry each block in hand one step: claim w_t
+            u64 wold = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (lane == v && have[v]) wold = atom_add_acq_rel(&wr[tgt[v]], 1ull << 32);
+            bool unp[V], emp[V];
+            u64 wslot[V];
+            bool any_unp = false;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const u64 o = __shfl_sync(0xffffffffu, wold, v);
+                unp[v] = emp[v] = false;
+                wslot[v] = 0;
+                if (have[v]) {
+                    const long long wt = (long long)(o >> 32);
+                    const long long rt = (long long)(u32)(o & 0xffffffffull) - (long long)kPtrBias;
+                    if (!IPS4O_GUARD(ws.ctr, wt >= 0 && (u64)wt < delim[tgt[v] + 1], wt, delim[tgt[v] + 1])) {
+                        failed = true;
+                    } else if (wt <= rt) {
+                        if (!IPS4O_GUARD(ws.ctr, (u64)wt < nbc, wt, nbc)) failed = true;
+                        unp[v] = true;
+                        any_unp = true;
+                    } else {
+                        emp[v] = true;
+                    }
+                    wslot[v] = (u64)wt;
+                }
+            }
+            if (failed) {
+                if (lane == 0) set_status(ws.ctr, kStatusInternal);
+                break;
+            }
+            if (any_unp) {
+#pragma unroll
+                for (int v = 0; v < V; ++v)
+                    if (unp[v]) {
+#pragma unroll
+                        for (int q = 0; q < EPL; ++q) tmpb[v][q] = A[wslot[v] * B + lane + 32 * q];
+                    }
+                int mybk = 0;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const K hk = __shfl_sync(0xffffffffu, T::key(tmpb[v][0]), 0);
+                    if (lane == v && unp[v]) mybk = classify_key<K>(hk, tree, spl, logL, eq);
+                }
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const u32 t2 = (u32)__shfl_sync(0xffffffffu, mybk, v);
+                    if (unp[v]) {
+                        if (!IPS4O_GUARD(ws.ctr, t2 < nb, t2, nb)) {
+                            failed = true;
+                        } else if (t2 == tgt[v]) {
+                            ++skipped;                 // already in its bucket: leave it
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < EPL; ++q) {
+                                A[wslot[v] * B + lane + 32 * q] = buf[v][q];
+                                buf[v][q] = tmpb[v][q];
+                            }
+                            tgt[v] = t2;
+                            ++moved;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                if (!emp[v]) continue;
+                // empty slot: wait until nobody reads from bucket t
+                u32 ok = 1;
+                if (lane == v) {
+                    u32 it = 0;
+                    while (ld_acquire(&readers[tgt[v]]) != 0) {
+                        if (++it > spin_limit) { ok = 0; break; }
+                        __nanosleep(64);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, v);
+                if (!ok) {
+                    if (lane == 0) set_status(ws.ctr, kStatusTimeout);
                     failed = true;
                     break;
                 }
+                if (wslot[v] < nbc) {
 #pragma unroll
-                for (int q = 0; q < EPL; ++q) buf[q] = A[(u64)r * B + lane + 32 * q];
-                __threadfence();
-                __syncwarp();
-                if (lane == 0) red_add_relaxed(&readers[p], ~0u);
-                // move the block until it lands in an empty slot
-                int t = classify_key<K>(__shfl_sync(0xffffffffu, T::key(buf[0]), 0), tree, spl, logL, eq);
-                for (;;) {
-                    if (lane == 0) old = atom_add_acq_rel(&wr[t], 1ull << 32);
-                    old = __shfl_sync(0xffffffffu, old, 0);
-                    const long long wt = (long long)(old >> 32);
-                    const long long rt = (long long)(u32)(old & 0xffffffffull) - (long long)kPtrBias;
-                    if ((u64)wt >= delim[t + 1]) {
-                        if (lane == 0) set_status(ws.ctr, kStatusInternal);
-                        failed = true;
-                        break;
-                    }
-                    if (wt <= rt) {
-                        // slot wt is unprocessed: swap unless its block already belongs to t
+                    for (int q = 0; q < EPL; ++q) A[wslot[v] * B + lane + 32 * q] = buf[v][q];
+                } else if (partial && wslot[v] == nbc) {
 #pragma unroll
-                        for (int q = 0; q < EPL; ++q) tmpb[q] = A[(u64)wt * B + lane + 32 * q];
-                        const int t2 = classify_key<K>(__shfl_sync(0xffffffffu, T::key(tmpb[0]), 0), tree, spl, logL, eq);
-                        if (t2 == t) {
-                            ++skipped;
-                            continue;
-                        }
-#pragma unroll
-                        for (int q = 0; q < EPL; ++q) {
-                            A[(u64)wt * B + lane + 32 * q] = buf[q];
-                            buf[q] = tmpb[q];
-                        }
-                        ++moved;
-                        t = t2;
-                        continue;
-                    }
-                    // slot wt is empty: wait until nobody reads from bucket t
-                    u32 ok = 1;
-                    if (lane == 0) {
-                        u32 it = 0;
-                        while (ld_acquire(&readers[t]) != 0) {
-                            if (++it > spin_limit) { ok = 0; break; }
-                            __nanosleep(64);
-                        }
-                    }
-                    ok = __shfl_sync(0xffffffffu, ok, 0);
-                    if (!ok) {
-                        if (lane == 0) set_status(ws.ctr, kStatusTimeout);
-                        failed = true;
-                        break;
-                    }
-                    if ((u64)wt < nbc) {
-#pragma unroll
-                        for (int q = 0; q < EPL; ++q) A[(u64)wt * B + lane + 32 * q] = buf[q];
-                    } else if (partial && (u64)wt == nbc) {
-#pragma unroll
-                        for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = buf[q];
-                    } else {
-                        if (lane == 0) set_status(ws.ctr, kStatusInternal);
-                        failed = true;
-                    }
-                    ++moved;
+                    for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = buf[v][q];
+                } else {
+                    if (lane == 0) set_status(ws.ctr, kStatusInternal);
+                    failed = true;
                     break;
                 }
-                if (failed) break;
+                have[v] = false;
+                ++moved;
             }
         }
     }
@@ -729,23 +796,26 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
 template <class T>
 struct CleanupCfg {
     typedef typename T::elem_t E;
-    static constexpr int TPB = 512;
+    static constexpr int TPB = BaseCfg<T>::TPB;
     static constexpr int B = T::kBlock;
-    static constexpr size_t off_sort = 0;
-    static constexpr size_t off_ov = off_sort + (size_t)T::kBaseCap * sizeof(E);
+    // the cleanup arrays and the base-case arrays share the dynamic shared
+    // memory: the base case starts only after the cleanup copy is complete
+    static constexpr size_t off_ov = 0;
     static constexpr size_t off_lpre = off_ov + (size_t)B * sizeof(E);
     static constexpr size_t off_src = off_lpre + (size_t)(kMaxStripesPerSub + 1) * 4 + 4;
-    static constexpr size_t smem_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
+    static constexpr size_t cleanup_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
+    static constexpr size_t smem_bytes =
+        cleanup_bytes > BaseCfg<T>::smem_bytes ? cleanup_bytes : BaseCfg<T>::smem_bytes;
 };
 
 template <class T>
-__global__ void __launch_bounds__(CleanupCfg<T>::TPB)
-    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 base_cap, u32 spin_limit, u32 partition_only) {
+__global__ void __launch_bounds__(CleanupCfg<T>::TPB, 2)
+    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 base_cap, u32 spin_limit, u32 partition_only,
+              u64 seed) {
     typedef typename T::elem_t E;
     typedef CleanupCfg<T> C;
     constexpr int TPB = C::TPB, B = C::B;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    E* s_sort = (E*)(smem_raw + C::off_sort);
     E* s_ov = (E*)(smem_raw + C::off_ov);
     u32* s_lpre = (u32*)(smem_raw + C::off_lpre);
     u64* s_src = (u64*)(smem_raw + C::off_src);
@@ -852,7 +922,7 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
     const bool is_eq = sub.eq && (b & 1);
     if (is_eq || size < 2) return;
     if (size <= base_cap) {
-        sort_range_in_smem<T, TPB>(A + Bb, size, s_sort);
+        cta_sort<T>(A + Bb, (u32)size, smem_raw, seed ^ mix64(sub.begin + Bb));
         if (threadIdx.x == 0) atomicAdd(&ws.ctr->base_buckets, 1ull);
     } else if (threadIdx.x == 0) {
         u32 idx = atomicAdd(&ws.ctr->next_count, 1u);

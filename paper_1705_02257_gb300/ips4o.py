@@ -34,8 +34,10 @@ PHASES = ("sample", "classify", "prefix", "empty_block_fix", "block_permutation"
 class Ips4oError(RuntimeError):
     def __init__(self, status: int, where: str):
         msg = f"{where}: {STATUS.get(status, status)}"
-        if status == 5:
-            msg += f" ({last_cuda_error()})"
+        if status in (5, 6, 7):
+            detail = last_cuda_error()
+            if detail:
+                msg += f" ({detail})"
         super().__init__(msg)
         self.status = status
 
