@@ -63,7 +63,8 @@ typedef enum {
     IPS4O_ERR_CUDA = 5,             /* a CUDA runtime call failed (see ips4o_last_cuda_error) */
     IPS4O_ERR_TIMEOUT = 6,          /* a bounded device-side wait gave up */
     IPS4O_ERR_INTERNAL = 7,         /* a device-side invariant check failed */
-    IPS4O_ERR_TOO_LARGE = 8         /* request exceeds a fixed capacity of the entry point */
+    IPS4O_ERR_TOO_LARGE = 8         /* request exceeds a fixed capacity of the entry point
+                                       (ips4o_sort: more than 16 GiB of elements per call) */
 } ips4o_status;
 
 /* Tuning parameters (Section 4.7 gives k <= 256, alpha = 0.2 log n,

@@ -94,7 +94,9 @@ static ips4o_status check_args(const void* p, size_t n, int kt) {
     if (kt < 0 || kt > IPS4O_REC100_K10) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (elem_size(kt) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (n > 1 && !p) return IPS4O_ERR_INVALID_ARG;
-    if (n > ((size_t)1 << 37)) return IPS4O_ERR_TOO_LARGE;   // block indices must fit 31 bits
+    // one bucket region of the block permutation holds at most 2^25 - 2^16 - 2
+    // blocks of 512 bytes (the packed pointer word): 16 GiB per call
+    if (n > ((size_t)16 << 30) / elem_size(kt)) return IPS4O_ERR_TOO_LARGE;
     if (p && ((uintptr_t)p % elem_size(kt)) != 0) return IPS4O_ERR_MISALIGNED;
     return IPS4O_OK;
 }

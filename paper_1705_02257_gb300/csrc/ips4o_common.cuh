@@ -18,7 +18,19 @@ typedef unsigned int u32;
 constexpr int kMaxBuckets = 256;      // buckets per step (ids fit one byte)
 constexpr int kMaxLeaves = 256;       // leaves of the implicit search tree
 constexpr int kMaxStripesPerSub = 1024;
-constexpr u32 kPtrBias = 0x80000000u; // r_i is stored biased so it may go below w_i - 1
+// Per-bucket pointer word of the block permutation (Section 4.2 keeps w_i
+// and r_i in one 128-bit word; here one 64-bit word also carries the reader
+// count): [w_i - d_i : 25 bits | r_i - d_i + kRBias : 25 bits | readers : 14 bits].
+// r_i is biased because failed claims may take it below w_i - 1.
+constexpr int kRdBits = 14;
+constexpr int kRBits = 25;
+constexpr int kWShift = kRdBits + kRBits;                 // 39
+constexpr unsigned long long kRBias = 1ull << 16;
+constexpr unsigned long long kClaimRead = 1ull - (1ull << kRdBits);   // readers + 1, r - 1
+constexpr unsigned long long kClaimWrite = 1ull << kWShift;          // w + 1
+constexpr unsigned long long kReadDone = ~0ull;                      // readers - 1
+constexpr unsigned long long kMaxRegionBlocks = (1ull << kRBits) - kRBias - 2;
+constexpr unsigned kMaxMoversPerSub = 12000;              // < 2^kRdBits concurrent readers
 
 // Device status word bits.
 constexpr u32 kStatusTimeout = 1u;     // a bounded wait gave up
@@ -133,8 +145,7 @@ struct Workspace {
     key_t* spl;               // [max_sub][256]   sorted splitters s_1..s_{L-1}
     u64* bstart;              // [max_sub][257]   bucket starts relative to sub begin
     u32* delim;               // [max_sub][257]   delimiter block indices d_i
-    u64* wr;                  // [max_sub][256]   packed (w_i << 32) | (r_i + bias)
-    u32* readers;             // [max_sub][256]   threads currently reading from bucket i
+    u64* wr;                  // [max_sub][256]   packed w_i, r_i, reader count (see kWShift)
     u32* flags;               // [max_sub][256]   cleanup hand-over flags
     u32* exhausted;           // [max_sub][8]     bitmap of buckets without unprocessed blocks
     u32* region_full;         // [max_sub][256]   full blocks inside region [d_i, d_{i+1})
@@ -180,6 +191,27 @@ __device__ __forceinline__ u64 atom_add_acq_rel(u64* p, u64 v) {
     asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
     return old;
 }
+__device__ __forceinline__ u64 atom_add_acquire(u64* p, u64 v) {
+    u64 old;
+    asm volatile("atom.acquire.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+    return old;
+}
+__device__ __forceinline__ u64 ld_acquire64(const u64* p) {
+    u64 v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_add_release64(u64* p, u64 v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_relaxed64(u64* p, u64 v) {
+    asm volatile("red.relaxed.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ u32 pk_readers(u64 x) { return (u32)(x & ((1ull << kRdBits) - 1)); }
+__device__ __forceinline__ long long pk_r(u64 x) {
+    return (long long)((x >> kRdBits) & ((1ull << kRBits) - 1)) - (long long)kRBias;
+}
+__device__ __forceinline__ long long pk_w(u64 x) { return (long long)(x >> kWShift); }
 __device__ __forceinline__ u32 ld_acquire(const u32* p) {
     u32 v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");

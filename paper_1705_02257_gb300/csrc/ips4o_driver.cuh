@@ -73,7 +73,6 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.bstart = (u64*)take(S * (kMaxBuckets + 1) * 8);
     w.delim = (u32*)take(S * (kMaxBuckets + 1) * 4);
     w.wr = (u64*)take(S * kMaxBuckets * 8);
-    w.readers = (u32*)take(S * kMaxBuckets * 4);
     w.flags = (u32*)take(S * kMaxBuckets * 4);
     w.exhausted = (u32*)take(S * 8 * 4);
     w.region_full = (u32*)take(S * kMaxBuckets * 4);

@@ -356,9 +356,9 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
         }
         const u32 holes = nfr - in_zone;
         delim[b] = d0;
-        const u64 r = (u64)d0 + nfr - 1 + kPtrBias;   // r_i = d_i + nfr - 1 (biased)
-        ws.wr[(u64)j * kMaxBuckets + b] = ((u64)d0 << 32) | (r & 0xffffffffull);
-        ws.readers[(u64)j * kMaxBuckets + b] = 0;
+        // w_i = d_i, r_i = d_i + nfr - 1 (the last full block of the region), no readers
+        if ((u64)(d1 - d0) > kMaxRegionBlocks) set_status(ws.ctr, kStatusCapacity);
+        ws.wr[(u64)j * kMaxBuckets + b] = (u64)((long long)nfr - 1 + (long long)kRBias) << kRdBits;
         ws.flags[(u64)j * kMaxBuckets + b] = 0;
         ws.region_full[(u64)j * kMaxBuckets + b] = nfr;
         ws.bucket_full[(u64)j * kMaxBuckets + b] = fb;
@@ -468,11 +468,16 @@ __global__ void __launch_bounds__(TPB) k_fix(typename T::elem_t* arr, Workspace<
 // primary bucket, takes unprocessed blocks from it by decrementing r_p, and
 // carries each block to its destination bucket t by incrementing w_t: a swap
 // with the unprocessed block found there (or a skip when that block already
-// belongs to t), or a write into an empty slot, after which it reads again.
-// (w_i, r_i) live in one 64-bit word updated with single atomic adds, so
-// every mover sees both pointers consistently.  A reader count per bucket
-// protects a block that has been claimed but not yet read: writes into
-// empty slots wait (boundedly) until no mover is reading from the bucket.
+// belongs to t, which leaves it in place), or a write into an empty slot,
+// after which it reads again.  When its primary bucket has no unprocessed
+// block left it moves to the next one; it stops when no bucket has any.
+//
+// w_i, r_i and the number of movers currently reading from bucket i share
+// one 64-bit word, so a claim is a single atomic add and every mover sees
+// the three consistently.  A block claimed for reading stays protected until
+// its reader drops the count with a release; a write into an empty slot
+// waits (boundedly) until the count it observed has drained.  Buckets found
+// empty are recorded in a bitmap so that movers stop probing them.
 //
 // Each warp runs V movers in lockstep: their pointer atomics, block loads
 // and block stores are issued by the same instructions, so one warp keeps
@@ -497,6 +502,9 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
     __shared__ u32 s_gpre[1025];
     __shared__ u64 s_tot;
     __shared__ u32 tmp[32];
+    __shared__ K s_tree[NW][kMaxLeaves];
+    __shared__ K s_spl[NW][kMaxLeaves];
+    __shared__ u32 s_delim[NW][kMaxBuckets + 1];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 G = gridDim.x * NW;                 // warps in the grid
     // mover groups (warps) per subproblem, in proportion to its full blocks
@@ -521,8 +529,10 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                     u64 x = (bl * (u64)G + total - 1) / total;
                     const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + V - 1) / V;
                     const u64 cap_k = (bl + V - 1) / V;
+                    const u64 cap_r = kMaxMoversPerSub / V;
                     x = x < cap_b ? x : cap_b;
                     x = x < cap_k ? x : cap_k;
+                    x = x < cap_r ? x : cap_r;
                     gv[q] = (u32)(x < 1 ? 1 : x);
                 }
             }
@@ -540,6 +550,9 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
         __syncthreads();
     }
     const u32 GT = s_gpre[nsub];
+    K* tree = s_tree[warp];
+    K* spl = s_spl[warp];
+    u32* delim = s_delim[warp];
     u64 moved = 0, skipped = 0;
     bool failed = false;
     for (u32 g = blockIdx.x * NW + warp; g < GT && !failed; g += G) {
@@ -552,17 +565,21 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
         const u32 nb = sub.nbuckets;
         const int logL = (int)sub.log_leaves;
         const bool eq = sub.eq != 0;
-        const K* tree = ws.tree + (u64)j * kMaxLeaves;
-        const K* spl = ws.spl + (u64)j * kMaxLeaves;
+        // this warp's copy of the subproblem's tree, splitters and delimiters
+        __syncwarp();
+        for (int i = lane; i < kMaxLeaves; i += 32) {
+            tree[i] = ws.tree[(u64)j * kMaxLeaves + i];
+            spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
+        }
+        for (int i = lane; i <= kMaxBuckets; i += 32) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
+        __syncwarp();
         u64* wr = ws.wr + (u64)j * kMaxBuckets;
-        u32* readers = ws.readers + (u64)j * kMaxBuckets;
-        const u32* delim = ws.delim + (u64)j * (kMaxBuckets + 1);
+        u32* exh = ws.exhausted + (u64)j * 8;
         E* A = arr + sub.begin;
         E* ovf = ws.overflow + (u64)j * B;
         const u64 nbc = sub.n / B;                   // complete block slots
         const bool partial = (sub.n % B) != 0;
 
-        u32* exh = ws.exhausted + (u64)j * 8;
         // per-mover state (arrays indexed by compile-time v only)
         E buf[V][EPL], tmpb[V][EPL];
         u32 prim[V], tgt[V];
@@ -582,46 +599,36 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
             for (int v = 0; v < V; ++v) any_active |= !done[v];
             if (!any_active || failed) break;
             // ---- movers with empty hands pick a primary bucket that still has
-            // unprocessed blocks (next one cyclically, as in Section 4.2)
-            bool want = false;
+            // unprocessed blocks (the next one cyclically, Section 4.2)
 #pragma unroll
-            for (int v = 0; v < V; ++v) want |= (!have[v] && !done[v]);
-            if (want) {
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (have[v] || done[v]) continue;
-                    // first non-exhausted bucket at or after prim (cyclic)
-                    const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
-                    // word index w relative to pw: lane l looks at word (pw + l) % 8 masked
-                    const u32 wi = (pw + (u32)lane) & 7u;
-                    const u32 word_l = __shfl_sync(0xffffffffu, exw, wi);     // all lanes shuffle
-                    const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
-                    u32 free_bits = 0u;
-                    if (lane < 8) free_bits = ~word_l;
-                    if (lane == 0) free_bits &= ~((1u << pb) - 1u);      // at or after prim in its word
-                    // wrap-around: bits before prim in word pw are checked last (lane 8)
-                    if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
-                    const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
-                    if (ball == 0) {
-                        done[v] = true;
-                        continue;
-                    }
-                    const int first = __ffs(ball) - 1;
-                    const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
-                    const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
-                    const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
-                    if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
-                    else { failed = true; done[v] = true; }
+            for (int v = 0; v < V; ++v) {
+                if (have[v] || done[v]) continue;
+                const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
+                // lane l < 8 looks at word (pw + l) % 8; lane 8 at the bits of
+                // word pw before prim (the end of the cycle)
+                const u32 word_l = __shfl_sync(0xffffffffu, exw, (pw + (u32)lane) & 7u);
+                const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
+                u32 free_bits = 0u;
+                if (lane < 8) free_bits = ~word_l;
+                if (lane == 0) free_bits &= ~((1u << pb) - 1u);
+                if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
+                const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
+                if (ball == 0) {
+                    done[v] = true;
+                    continue;
                 }
+                const int first = __ffs(ball) - 1;
+                const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
+                const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
+                const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
+                if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
+                else { failed = true; done[v] = true; }
             }
-            // ---- take a block from the primary bucket: r_p--
+            // ---- take a block from the primary bucket: readers + 1, r_p - 1
             u64 aold = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                if (lane == v && !have[v] && !done[v]) {
-                    red_add_relaxed(&readers[prim[v]], 1u);
-                    aold = atom_add_acq_rel(&wr[prim[v]], ~0ull);
-                }
+                if (lane == v && !have[v] && !done[v]) aold = atomicAdd(&wr[prim[v]], kClaimRead);
             bool got[V];
             u64 rslot[V];
             bool any_got = false, any_exh = false;
@@ -631,28 +638,26 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                 got[v] = false;
                 rslot[v] = 0;
                 if (!have[v] && !done[v]) {
-                    const long long w = (long long)(o >> 32);
-                    const long long r = (long long)(u32)(o & 0xffffffffull) - (long long)kPtrBias;
+                    const long long w = pk_w(o), r = pk_r(o);
                     if (r < w) {
+                        // no unprocessed block left: undo the reader count
                         if (lane == v) {
-                            red_add_relaxed(&readers[prim[v]], ~0u);
+                            red_add_relaxed64(&wr[prim[v]], kReadDone);
                             atomicOr(&exh[prim[v] >> 5], 1u << (prim[v] & 31));
                         }
                         any_exh = true;
-                    } else if (!IPS4O_GUARD(ws.ctr, r >= 0 && (u64)(r + 1) * B <= nbc * B, r, nbc)) {
-                        if (lane == v) red_add_relaxed(&readers[prim[v]], ~0u);
+                    } else if (!IPS4O_GUARD(ws.ctr, r >= 0 && (u64)delim[prim[v]] + r < nbc,
+                                            (u64)delim[prim[v]] + r, nbc)) {
+                        if (lane == v) red_add_relaxed64(&wr[prim[v]], kReadDone);
                         failed = true;
                     } else {
                         got[v] = true;
-                        rslot[v] = (u64)r;
+                        rslot[v] = (u64)delim[prim[v]] + (u64)r;
                         any_got = true;
                     }
                 }
             }
-            if (failed) {
-                if (lane == 0) set_status(ws.ctr, kStatusInternal);
-                break;
-            }
+            if (failed) break;
             if (any_exh) {
                 __syncwarp();
                 if (lane < 8) exw = ld_relaxed(&exh[lane]);
@@ -670,14 +675,14 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                     const K hk = __shfl_sync(0xffffffffu, T::key(buf[v][0]), 0);
                     if (lane == v && got[v]) mybk = classify_key<K>(hk, tree, spl, logL, eq);
                 }
-                // the warp barrier orders every lane's block loads before the
-                // release decrement of the reader count (release is cumulative),
-                // so a writer that sees the count drop cannot overwrite a slot
-                // still being read
+                // The warp barrier orders every lane's block loads before the
+                // release that drops the reader count (release is cumulative):
+                // a writer that sees the count drained cannot overwrite a slot
+                // that is still being read.
                 __syncwarp();
 #pragma unroll
                 for (int v = 0; v < V; ++v)
-                    if (lane == v && got[v]) red_add_release(&readers[prim[v]], ~0u);
+                    if (lane == v && got[v]) red_add_release64(&wr[prim[v]], kReadDone);
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
                     const int t = __shfl_sync(0xffffffffu, mybk, v);
@@ -686,39 +691,42 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                         else failed = true;
                     }
                 }
+                if (failed) break;
             }
-            // ---- carry each block in hand one step: claim w_t
+            // ---- carry each block in hand one step: w_t + 1
             u64 wold = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                if (lane == v && have[v]) wold = atom_add_acq_rel(&wr[tgt[v]], 1ull << 32);
+                if (lane == v && have[v]) wold = atom_add_acquire(&wr[tgt[v]], kClaimWrite);
             bool unp[V], emp[V];
             u64 wslot[V];
+            u32 rd[V];
             bool any_unp = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 const u64 o = __shfl_sync(0xffffffffu, wold, v);
                 unp[v] = emp[v] = false;
                 wslot[v] = 0;
+                rd[v] = pk_readers(o);
                 if (have[v]) {
-                    const long long wt = (long long)(o >> 32);
-                    const long long rt = (long long)(u32)(o & 0xffffffffull) - (long long)kPtrBias;
-                    if (!IPS4O_GUARD(ws.ctr, wt >= 0 && (u64)wt < delim[tgt[v] + 1], wt, delim[tgt[v] + 1])) {
+                    const long long wt = pk_w(o), rt = pk_r(o);
+                    const u64 slot = (u64)delim[tgt[v]] + (u64)wt;
+                    if (!IPS4O_GUARD(ws.ctr, slot < delim[tgt[v] + 1], slot, delim[tgt[v] + 1])) {
                         failed = true;
                     } else if (wt <= rt) {
-                        if (!IPS4O_GUARD(ws.ctr, (u64)wt < nbc, wt, nbc)) failed = true;
-                        unp[v] = true;
-                        any_unp = true;
+                        if (IPS4O_GUARD(ws.ctr, slot < nbc, slot, nbc)) {
+                            unp[v] = true;
+                            any_unp = true;
+                        } else {
+                            failed = true;
+                        }
                     } else {
                         emp[v] = true;
                     }
-                    wslot[v] = (u64)wt;
+                    wslot[v] = slot;
                 }
             }
-            if (failed) {
-                if (lane == 0) set_status(ws.ctr, kStatusInternal);
-                break;
-            }
+            if (failed) break;
             if (any_unp) {
 #pragma unroll
                 for (int v = 0; v < V; ++v)
@@ -751,15 +759,17 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                         }
                     }
                 }
+                if (failed) break;
             }
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 if (!emp[v]) continue;
-                // empty slot: wait until nobody reads from bucket t
+                // empty slot: if a mover was reading from bucket t when the slot
+                // was claimed, wait until the count drains
                 u32 ok = 1;
-                if (lane == v) {
+                if (lane == v && rd[v] != 0) {
                     u32 it = 0;
-                    while (ld_acquire(&readers[tgt[v]]) != 0) {
+                    while (pk_readers(ld_acquire64(&wr[tgt[v]])) != 0) {
                         if (++it > spin_limit) { ok = 0; break; }
                         __nanosleep(64);
                     }
@@ -777,7 +787,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
 #pragma unroll
                     for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = buf[v][q];
                 } else {
-                    if (lane == 0) set_status(ws.ctr, kStatusInternal);
+                    IPS4O_GUARD(ws.ctr, false, wslot[v], nbc);
                     failed = true;
                     break;
                 }
@@ -833,7 +843,7 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB, 2)
     const u64* bstart = ws.bstart + (u64)j * (kMaxBuckets + 1);
     const u64 Bb = bstart[b], Eb = bstart[b + 1];
     const u32 d0 = ws.delim[(u64)j * (kMaxBuckets + 1) + b];
-    const u64 w = ws.wr[(u64)j * kMaxBuckets + b] >> 32;
+    const u64 w = (u64)d0 + (u64)pk_w(ws.wr[(u64)j * kMaxBuckets + b]);
     const u64 nbc = sub.n / B;
     const bool partial = (sub.n % B) != 0;
     const bool has_blocks = w > d0;
