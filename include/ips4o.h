@@ -74,7 +74,8 @@ typedef struct {
     int k_max;            /* maximum buckets per distribution step, power of two in [4, 256]; default 256 */
     int alpha;            /* oversampling factor; <= 0 selects the default (max(8, 0.2 log2 n) ... see source) */
     int base_case_max;    /* buckets of at most this many elements are sorted in shared memory
-                             (clamped to the per-type capacity); <= 0 selects the default */
+                             (clamped to [16, ips4o_base_case_capacity]); smaller values force
+                             deeper recursion; <= 0 selects the capacity */
     int stripes_per_sm;   /* stripes (local-classification work items) per SM for a level; default 2 */
     int profile;          /* 1: time every kernel with CUDA events into ips4o_stats.phase_ms */
     uint64_t seed;        /* sampling seed */

@@ -87,41 +87,36 @@ __device__ void select_splitters(const K* keys, u32 kk, u32 alpha, K* cand, u32*
     *eq_out = eq;
 }
 
-template <class T>
+template <class T, int TPB_, int CAP_>
 struct BaseCfg {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    static constexpr int TPB = 512;
+    static constexpr int TPB = TPB_;
     static constexpr int NW = TPB / 32;
-    static constexpr int CAP = T::kBaseCap;
+    static constexpr int CAP = CAP_;
     static constexpr int EPT = CAP / TPB;
-    static constexpr int MAXSUB = 512;       // sub-buckets of the on-chip distribution
-    static constexpr int N0 = 8;             // target sub-bucket size
+    static constexpr int N0 = 4;             // target sub-bucket size
+    static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
     static constexpr int LIMIT = 64;         // any larger sub-bucket: whole-bucket bitonic fallback
     static constexpr size_t off_data = 0;
     static constexpr size_t off_cnt = off_data + (size_t)CAP * sizeof(E);
     static constexpr size_t off_off = off_cnt + MAXSUB * 4;
     static constexpr size_t off_tmp = off_off + MAXSUB * 4;
     static constexpr size_t smem_bytes = off_tmp + 64 * 8;
+    static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
-    static_assert(CAP < 65536, "ranks are packed in 16 bits");
-    static_assert(MAXSUB <= TPB, "one scan entry per thread");
+    static_assert(CAP <= 65535, "ranks are packed in 16 bits");
+    static_assert(EPT % 2 == 0, "ranks are packed two per register");
+    static_assert(MAXSUB % TPB == 0, "whole sub-bucket counters per thread");
 };
 
+// The two size classes: most buckets (at most kBaseSmall elements) are
+// sorted by 512-thread CTAs that fit two per SM; the rare larger ones (up to
+// kBaseCap) by 1024-thread CTAs with 128 KiB of shared memory.
 template <class T>
-__device__ __forceinline__ void insertion_sort(typename T::elem_t* a, u32 n) {
-    typedef typename T::elem_t E;
-    for (u32 i = 1; i < n; ++i) {
-        const E x = a[i];
-        const typename T::key_t kx = T::key(x);
-        u32 j = i;
-        while (j > 0 && kx < T::key(a[j - 1])) {
-            a[j] = a[j - 1];
-            --j;
-        }
-        a[j] = x;
-    }
-}
+using BaseSmall = BaseCfg<T, 512, T::kBaseSmall>;
+template <class T>
+using BaseLarge = BaseCfg<T, 1024, T::kBaseCap>;
 
 // In-place sort of s[0..n) in shared memory by the whole CTA: a bitonic
 // network whose merge stages start by comparing element i with its mirror
@@ -156,22 +151,22 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 
 // Sort g[0..m), m <= CAP, with the whole CTA (BaseCfg<T>::TPB threads).
 //
-// The bucket is read once into registers (and a shared-memory copy).  Its
-// key range [lo, hi] is split into KB equal sub-ranges, KB about m / 8, and
-// every element goes to sub-bucket floor((key - lo) * KB / (hi - lo + 1))
-// (one 64-bit multiply-high); a bucket produced by the sampled distribution
-// steps is close to uniform over its range, so the sub-buckets are small.
-// After a counting-sort scatter in shared memory each sub-bucket is
-// finished by insertion sort.  If some sub-bucket exceeds LIMIT elements
-// (clustered keys), the whole bucket is sorted by a bitonic network
-// instead, so the cost stays bounded for any input.
-template <class T>
-__device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem, u64 seed) {
-    typedef BaseCfg<T> C;
+// The bucket is read once into registers.  Its key range [lo, hi] is split
+// into KB equal sub-ranges, KB about m / 4, and every element goes to
+// sub-bucket floor((key - lo) * KB / (hi - lo + 1)) (one 64-bit
+// multiply-high); a bucket produced by the sampled distribution steps is
+// close to uniform over its range, so the sub-buckets are small.  After a
+// counting-sort scatter into shared memory, each element's final position is
+// the start of its sub-bucket plus the number of keys of that sub-bucket
+// that are smaller (or equal and earlier), and it is written there directly.
+// If some sub-bucket exceeds LIMIT elements (clustered keys), the whole
+// bucket is sorted by a bitonic network instead, so the cost stays bounded
+// for any input.
+template <class T, class C>
+__device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    constexpr int TPB = C::TPB, EPT = C::EPT;
-    (void)seed;
+    constexpr int TPB = C::TPB, EPT = C::EPT, SPT = C::SUBS_PER_THREAD;
     if (m < 2) return;
     E* data = (E*)(smem + C::off_data);
     u32* cnt = (u32*)(smem + C::off_cnt);
@@ -186,13 +181,13 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem, u64 
         const u32 idx = tid + q * TPB;
         if (idx < m) {
             e[q] = g[idx];
-            data[idx] = e[q];
             const K k = T::key(e[q]);
             lo = k < lo ? k : lo;
             hi = k > hi ? k : hi;
         }
     }
-    if (tid < C::MAXSUB) cnt[tid] = 0;
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) cnt[tid * SPT + q] = 0;
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -219,57 +214,95 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem, u64 
     // floor(2^64 / (range + 1)) * KB, without dividing by zero when the
     // bucket spans the whole 64-bit key range
     const u64 mult = direct ? 0 : (range == ~0ull ? (u64)KB : (~0ull / (range + 1)) * KB);
-    u32 br[EPT];
+    auto sub_of = [&](const K& k) -> u32 {
+        const u64 d = (u64)(k - lo);
+        const u32 b = direct ? (u32)d : (u32)__umul64hi(d, mult);
+        return b < KB ? b : KB - 1;
+    };
+    u32 rk2[EPT / 2];
+#pragma unroll
+    for (int q = 0; q < EPT / 2; ++q) rk2[q] = 0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
         if (idx < m) {
-            const u64 d = (u64)(T::key(e[q]) - lo);
-            u32 b = direct ? (u32)d : (u32)__umul64hi(d, mult);
-            b = b < KB ? b : KB - 1;                   // cannot trigger; keeps the index in range
-            br[q] = (b << 16) | atomicAdd(&cnt[b], 1u);
+            const u32 r = atomicAdd(&cnt[sub_of(T::key(e[q]))], 1u);
+            rk2[q / 2] |= r << (16 * (q & 1));
         }
     }
     __syncthreads();
-    const u32 c = (u32)tid < (u32)C::MAXSUB ? cnt[tid] : 0u;
-    const int big = __syncthreads_or(c > (u32)C::LIMIT ? 1 : 0);
-    if (big) {
-        // clustered keys: the copy in shared memory is sorted as a whole
-        cta_bitonic<T, TPB>(data, m);
-    } else {
-        u32 tot;
-        const u32 pre = block_exclusive_scan<u32>(c, (u32*)tmp, &tot);
-        if ((u32)tid < (u32)C::MAXSUB) off[tid] = pre;
-        __syncthreads();
+    // exclusive scan of the sub-bucket sizes (SPT consecutive entries per thread)
+    u32 c[SPT], csum = 0, cmax = 0;
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const u32 idx = tid + q * TPB;
-            if (idx < m) data[off[br[q] >> 16] + (br[q] & 0xffffu)] = e[q];
-        }
-        __syncthreads();
-        if ((u32)tid < KB && c > 1) insertion_sort<T>(data + off[tid], c);
-        __syncthreads();
+    for (int q = 0; q < SPT; ++q) {
+        c[q] = cnt[tid * SPT + q];
+        csum += c[q];
+        cmax = c[q] > cmax ? c[q] : cmax;
     }
+    const int big = __syncthreads_or(cmax > (u32)C::LIMIT ? 1 : 0);
+    u32 tot;
+    u32 pre = block_exclusive_scan<u32>(csum, (u32*)tmp, &tot);
+#pragma unroll
+    for (int q = 0; q < SPT; ++q) {
+        off[tid * SPT + q] = pre;
+        pre += c[q];
+    }
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
-        if (idx < m) g[idx] = data[idx];
+        if (idx < m) {
+            const u32 r = (rk2[q / 2] >> (16 * (q & 1))) & 0xffffu;
+            data[off[sub_of(T::key(e[q]))] + r] = e[q];
+        }
+    }
+    __syncthreads();
+    if (big) {
+        // clustered keys: sort the whole bucket with a bitonic network
+        cta_bitonic<T, TPB>(data, m);
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const u32 idx = tid + q * TPB;
+            if (idx < m) g[idx] = data[idx];
+        }
+    } else {
+        // final position = sub-bucket start + rank of the key within it
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+            const u32 i = tid + q * TPB;
+            if (i < m) {
+                const E x = data[i];
+                const K k = T::key(x);
+                const u32 sb = sub_of(k);
+                const u32 o = off[sb], n_sb = cnt[sb];
+                u32 r = 0;
+                for (u32 jj = o; jj < o + n_sb; ++jj) {
+                    const K kj = T::key(data[jj]);
+                    r += (kj < k || (kj == k && jj < i)) ? 1u : 0u;
+                }
+                g[o + r] = x;
+            }
+        }
     }
     __syncthreads();
 }
 
-// Whole small inputs or segments: one CTA per segment.
-template <class T>
-__global__ void __launch_bounds__(BaseCfg<T>::TPB, 2) k_base(typename T::elem_t* arr, const Task* segs, u32 nseg,
-                                                          ChunkCounters* ctr, u64 seed) {
+// Base-case tasks (buckets or whole small inputs): a persistent grid takes
+// tasks i = blockIdx.x, blockIdx.x + gridDim.x, ... of the list; the count is
+// read from device memory, so the launch does not depend on the host.
+template <class T, class C>
+__global__ void __launch_bounds__(C::TPB, (C::TPB <= 512 ? 2 : 1))
+    k_base(typename T::elem_t* arr, const Task* tasks, const u32* count, ChunkCounters* ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    for (u32 i = blockIdx.x; i < nseg; i += gridDim.x) {
-        const Task t = segs[i];
-        if (t.n > (u64)BaseCfg<T>::CAP) {
-            if (threadIdx.x == 0) set_status(ctr, kStatusInternal);
-            continue;
-        }
-        cta_sort<T>(arr + t.begin, (u32)t.n, smem_raw, seed ^ mix64(t.begin));
+    const u32 n = *count;
+    for (u32 i = blockIdx.x; i < n; i += gridDim.x) {
+        const Task t = tasks[i];
+        if (!IPS4O_GUARD(ctr, t.n <= (u64)C::CAP, t.n, C::CAP)) continue;
+        cta_sort<T, C>(arr + t.begin, (u32)t.n, smem_raw);
+    }
+    if (threadIdx.x == 0 && blockIdx.x < n) {
+        const u32 mine = (n - blockIdx.x + gridDim.x - 1) / gridDim.x;
+        atomicAdd(&ctr->base_buckets, (u64)mine);
     }
 }
 

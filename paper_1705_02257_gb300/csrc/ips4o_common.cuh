@@ -48,7 +48,8 @@ struct TU64 {
     typedef u64 key_t;
     static constexpr int kId = 0;
     static constexpr int kBlock = 64;                 // 64 x 8 B = 512 B
-    static constexpr int kBaseCap = 8192;              // shared-memory base case capacity
+    static constexpr int kBaseSmall = 8192;            // base case size class sorted by 512-thread CTAs
+    static constexpr int kBaseCap = 16384;             // largest bucket sorted in shared memory (128 KiB)
     __host__ __device__ static inline key_t key(const elem_t& e) { return e; }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
 };
@@ -58,7 +59,8 @@ struct TF64 {
     typedef u64 key_t;      // order-preserving map of the bits
     static constexpr int kId = 1;
     static constexpr int kBlock = 64;
-    static constexpr int kBaseCap = 8192;
+    static constexpr int kBaseSmall = 8192;
+    static constexpr int kBaseCap = 16384;
     __host__ __device__ static inline key_t key(const elem_t& e) {
         return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
     }
@@ -75,7 +77,8 @@ struct TPair {
     typedef u64 key_t;
     static constexpr int kId = 2;
     static constexpr int kBlock = 32;                 // 32 x 16 B = 512 B
-    static constexpr int kBaseCap = 4096;
+    static constexpr int kBaseSmall = 4096;
+    static constexpr int kBaseCap = 8192;
     __host__ __device__ static inline key_t key(const elem_t& e) { return e.k; }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
 };
@@ -128,6 +131,8 @@ struct ChunkCounters {
     u32 guard_hits;     // number of failed bounds guards
     u32 pad;
     u64 guard_a, guard_b;   // operands of the first failed guard
+    u32 base_small;     // base-case tasks of the small size class
+    u32 base_large;     // base-case tasks of the large size class
     u64 blocks_moved;
     u64 blocks_skipped;
     u64 fix_blocks;
@@ -157,6 +162,8 @@ struct Workspace {
     elem_t* pool;             // [pool_cap]        partially filled buffer blocks (leftovers)
     elem_t* overflow;         // [max_sub][b]      overflow block per subproblem
     Task* next_tasks;         // [next_cap]
+    Task* base_small;         // [max_sub * 256] buckets for the small base case
+    Task* base_large;         // [max_sub * 256] buckets for the large base case
     ChunkCounters* ctr;       // [1]
     u32 max_sub, max_stripes;
     u64 pool_cap, next_cap;

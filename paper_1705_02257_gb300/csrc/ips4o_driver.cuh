@@ -35,9 +35,17 @@ struct Caps {
     u64 pool_cap, next_cap;
 };
 
+// Base-case threshold in effect: buckets larger than this recurse.
 template <class T>
-Caps<T> caps_for(u64 n, int sms, int stripes_per_sm) {
-    const u64 B = T::kBlock, cap = T::kBaseCap;
+u32 recursion_cap(const ips4o_params& p) {
+    u32 rc = (u32)T::kBaseCap;
+    if (p.base_case_max > 0) rc = std::min(rc, (u32)std::max(p.base_case_max, 16));
+    return rc;
+}
+
+template <class T>
+Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
+    const u64 B = T::kBlock;
     Caps<T> c;
     u64 target = (u64)std::max(1, stripes_per_sm) * (u64)std::max(1, sms);
     c.max_sub = (u32)std::min<u64>(1024, n / (cap + 1) + 1);
@@ -84,6 +92,8 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.pool = (E*)take(c.pool_cap * sizeof(E));
     w.overflow = (E*)take(S * T::kBlock * sizeof(E));
     w.next_tasks = (Task*)take(c.next_cap * sizeof(Task));
+    w.base_small = (Task*)take(S * kMaxBuckets * sizeof(Task));
+    w.base_large = (Task*)take(S * kMaxBuckets * sizeof(Task));
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.max_sub = c.max_sub;
     w.max_stripes = c.max_stripes;
@@ -103,7 +113,7 @@ size_t host_stage_bytes(const Caps<T>& c) {
 
 template <class T>
 size_t workspace_bytes_t(size_t n, int sms) {
-    Caps<T> c = caps_for<T>(n, sms, global_params().stripes_per_sm);
+    Caps<T> c = caps_for<T>(n, sms, global_params().stripes_per_sm, recursion_cap<T>(global_params()));
     return carve<T>(c, nullptr, nullptr);
 }
 
@@ -147,7 +157,8 @@ struct Driver {
     StripeDesc* h_stripes;
     ChunkCounters* h_ctr;
     Task* h_tasks;
-    u32 base_cap;
+    u32 base_cap;       // buckets average about half of this after the last step
+    u32 rec_cap;        // buckets larger than this recurse; smaller go to the base case
     u32 k_max;
     int permute_grid = 0;
     int next_event = 0;
@@ -157,7 +168,7 @@ struct Driver {
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
 
     ips4o_status setup(u64 n) {
-        caps = caps_for<T>(n, st.sms, prm.stripes_per_sm);
+        caps = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
         const size_t need = carve<T>(caps, nullptr, nullptr);
         ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
         if (rc != IPS4O_OK) return rc;
@@ -172,8 +183,9 @@ struct Driver {
         h_ctr = (ChunkCounters*)h;
         h += align_up(sizeof(ChunkCounters), 256);
         h_tasks = (Task*)h;
-        base_cap = (u32)T::kBaseCap;
-        if (prm.base_case_max > 0) base_cap = std::min<u32>(base_cap, (u32)std::max(prm.base_case_max, 16));
+        // a smaller base case than the capacity forces deeper recursion
+        rec_cap = recursion_cap<T>(prm);
+        base_cap = std::min((u32)T::kBaseSmall, rec_cap);
         k_max = (u32)std::min(256, std::max(4, prm.k_max));
         k_max = pow2_ceil_host(k_max);
         if (k_max > 256) k_max = 256;
@@ -181,8 +193,10 @@ struct Driver {
                                         (int)ClassifyCfg<T>::smem_bytes));
         IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)CleanupCfg<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)BaseCfg<T>::smem_bytes));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseSmall<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)BaseSmall<T>::smem_bytes));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)BaseLarge<T>::smem_bytes));
         int occ = 0;
         IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB, 0));
         permute_grid = std::max(1, occ) * st.sms;
@@ -250,14 +264,24 @@ struct Driver {
     // Small input: one shared-memory sort.
     ips4o_status base_only(E* d, u64 n) {
         h_tasks[0] = Task{0, n};
-        IPS4O_CUDA(cudaMemcpyAsync(ws.next_tasks, h_tasks, sizeof(Task), cudaMemcpyHostToDevice, stream));
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
-        IPS4O_LAUNCH(6, (k_base<T><<<1, BaseCfg<T>::TPB, BaseCfg<T>::smem_bytes, stream>>>(d, ws.next_tasks, 1u, ws.ctr,
-                                                                                             prm.seed)));
+        const bool small = n <= (u64)T::kBaseSmall;
+        Task* list = small ? ws.base_small : ws.base_large;
+        u32* cnt = small ? &ws.ctr->base_small : &ws.ctr->base_large;
+        const u32 one = 1;
+        IPS4O_CUDA(cudaMemcpyAsync(list, h_tasks, sizeof(Task), cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemcpyAsync(cnt, &one, sizeof(u32), cudaMemcpyHostToDevice, stream));
+        if (small) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                                d, list, cnt, ws.ctr)));
+        } else {
+            IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<1, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                                d, list, cnt, ws.ctr)));
+        }
         IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
         IPS4O_CUDA(cudaStreamSynchronize(stream));
         IPS4O_CUDA(cudaGetLastError());
-        st.stats.base_case_buckets += 1;
+        st.stats.base_case_buckets += h_ctr->base_buckets;
         ips4o_status rc = collect_events();
         if (rc != IPS4O_OK) return rc;
         return status_from(h_ctr->status);
@@ -334,7 +358,13 @@ struct Driver {
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, 0, stream>>>(d, ws, nsub, kSpinLimit)));
         IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * kMaxBuckets, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nsub, base_cap, kSpinLimit, partition ? 1u : 0u, seed)));
+                            d, ws, nsub, kSpinLimit, partition ? 1u : 0u, rec_cap)));
+        if (!partition) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                                d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+            IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<st.sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                                d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+        }
         IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
         IPS4O_CUDA(cudaStreamSynchronize(stream));
         IPS4O_CUDA(cudaGetLastError());
@@ -356,7 +386,7 @@ struct Driver {
         ips4o_status rc = setup(n);
         if (rc != IPS4O_OK) return rc;
         st.stats.n = n;
-        if (!part && n <= base_cap) return base_only(d, n);
+        if (!part && n <= (u64)rec_cap) return base_only(d, n);
         std::vector<Task> level_tasks{Task{0, n}}, next;
         u32 level = 0;
         while (!level_tasks.empty()) {

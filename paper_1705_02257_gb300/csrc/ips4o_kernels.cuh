@@ -486,14 +486,14 @@ template <class T>
 struct PermuteCfg {
     static constexpr int TPB = 256;
     static constexpr int NW = TPB / 32;
-    static constexpr int V = 4;                  // movers per warp
+    static constexpr int V = 8;                  // movers per warp
     static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block
     static constexpr int MAX_MOVERS_PER_BUCKET = 64;
     static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
 };
 
 template <class T>
-__global__ void __launch_bounds__(PermuteCfg<T>::TPB)
+__global__ void __launch_bounds__(PermuteCfg<T>::TPB, 2)
     k_permute(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
@@ -505,6 +505,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
     __shared__ K s_tree[NW][kMaxLeaves];
     __shared__ K s_spl[NW][kMaxLeaves];
     __shared__ u32 s_delim[NW][kMaxBuckets + 1];
+    __shared__ E s_hand[NW][V][B];               // the block each mover carries
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const u32 G = gridDim.x * NW;                 // warps in the grid
     // mover groups (warps) per subproblem, in proportion to its full blocks
@@ -580,8 +581,11 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
         const u64 nbc = sub.n / B;                   // complete block slots
         const bool partial = (sub.n % B) != 0;
 
-        // per-mover state (arrays indexed by compile-time v only)
-        E buf[V][EPL], tmpb[V][EPL];
+        // per-mover state (arrays indexed by compile-time v only); the block a
+        // mover carries lives in shared memory, only freshly loaded blocks in
+        // registers
+        E (*hand)[B] = s_hand[warp];
+        E ldv[V][EPL];
         u32 prim[V], tgt[V];
         bool have[V], done[V];
 #pragma unroll
@@ -593,185 +597,92 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
         }
         // lanes 0..7 hold one word each of the exhausted-bucket bitmap
         u32 exw = lane < 8 ? ld_relaxed(&exh[lane]) : 0xffffffffu;
+        // One step per mover and iteration: a mover with empty hands claims a
+        // block of its primary bucket (readers + 1, r_p - 1) and loads it; a
+        // mover holding a block claims slot w_t of its destination and loads
+        // the block found there if it is unprocessed.  So every iteration costs
+        // one atomic and one load round trip for all V movers together.
         for (;;) {
             bool any_active = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) any_active |= !done[v];
             if (!any_active || failed) break;
-            // ---- movers with empty hands pick a primary bucket that still has
-            // unprocessed blocks (the next one cyclically, Section 4.2)
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (have[v] || done[v]) continue;
-                const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
-                // lane l < 8 looks at word (pw + l) % 8; lane 8 at the bits of
-                // word pw before prim (the end of the cycle)
-                const u32 word_l = __shfl_sync(0xffffffffu, exw, (pw + (u32)lane) & 7u);
-                const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
-                u32 free_bits = 0u;
-                if (lane < 8) free_bits = ~word_l;
-                if (lane == 0) free_bits &= ~((1u << pb) - 1u);
-                if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
-                const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
-                if (ball == 0) {
-                    done[v] = true;
-                    continue;
-                }
-                const int first = __ffs(ball) - 1;
-                const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
-                const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
-                const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
-                if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
-                else { failed = true; done[v] = true; }
-            }
-            // ---- take a block from the primary bucket: readers + 1, r_p - 1
-            u64 aold = 0;
+            u64 old = 0;
 #pragma unroll
             for (int v = 0; v < V; ++v)
-                if (lane == v && !have[v] && !done[v]) aold = atomicAdd(&wr[prim[v]], kClaimRead);
-            bool got[V];
-            u64 rslot[V];
-            bool any_got = false, any_exh = false;
+                if (lane == v && !done[v]) {
+                    if (have[v]) old = atom_add_acquire(&wr[tgt[v]], kClaimWrite);
+                    else old = atomicAdd(&wr[prim[v]], kClaimRead);
+                }
+            bool ldn[V], ldt[V], emp[V], exd[V];
+            u64 slot[V];
+            u32 rd[V];
+            bool any_exd = false;
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                const u64 o = __shfl_sync(0xffffffffu, aold, v);
-                got[v] = false;
-                rslot[v] = 0;
-                if (!have[v] && !done[v]) {
-                    const long long w = pk_w(o), r = pk_r(o);
+                const u64 o = __shfl_sync(0xffffffffu, old, v);
+                ldn[v] = ldt[v] = emp[v] = exd[v] = false;
+                slot[v] = 0;
+                rd[v] = pk_readers(o);
+                if (done[v]) continue;
+                const long long w = pk_w(o), r = pk_r(o);
+                if (!have[v]) {
                     if (r < w) {
-                        // no unprocessed block left: undo the reader count
+                        // no unprocessed block left in the primary bucket
                         if (lane == v) {
                             red_add_relaxed64(&wr[prim[v]], kReadDone);
                             atomicOr(&exh[prim[v] >> 5], 1u << (prim[v] & 31));
                         }
-                        any_exh = true;
-                    } else if (!IPS4O_GUARD(ws.ctr, r >= 0 && (u64)delim[prim[v]] + r < nbc,
-                                            (u64)delim[prim[v]] + r, nbc)) {
-                        if (lane == v) red_add_relaxed64(&wr[prim[v]], kReadDone);
-                        failed = true;
+                        exd[v] = true;
+                        any_exd = true;
                     } else {
-                        got[v] = true;
-                        rslot[v] = (u64)delim[prim[v]] + (u64)r;
-                        any_got = true;
-                    }
-                }
-            }
-            if (failed) break;
-            if (any_exh) {
-                __syncwarp();
-                if (lane < 8) exw = ld_relaxed(&exh[lane]);
-            }
-            if (any_got) {
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (got[v]) {
-#pragma unroll
-                        for (int q = 0; q < EPL; ++q) buf[v][q] = A[rslot[v] * B + lane + 32 * q];
-                    }
-                int mybk = 0;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const K hk = __shfl_sync(0xffffffffu, T::key(buf[v][0]), 0);
-                    if (lane == v && got[v]) mybk = classify_key<K>(hk, tree, spl, logL, eq);
-                }
-                // The warp barrier orders every lane's block loads before the
-                // release that drops the reader count (release is cumulative):
-                // a writer that sees the count drained cannot overwrite a slot
-                // that is still being read.
-                __syncwarp();
-#pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (lane == v && got[v]) red_add_release64(&wr[prim[v]], kReadDone);
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const int t = __shfl_sync(0xffffffffu, mybk, v);
-                    if (got[v]) {
-                        if (IPS4O_GUARD(ws.ctr, t >= 0 && (u32)t < nb, t, nb)) { have[v] = true; tgt[v] = (u32)t; }
+                        slot[v] = (u64)delim[prim[v]] + (u64)r;
+                        if (IPS4O_GUARD(ws.ctr, r >= 0 && slot[v] < nbc, slot[v], nbc)) ldn[v] = true;
                         else failed = true;
                     }
-                }
-                if (failed) break;
-            }
-            // ---- carry each block in hand one step: w_t + 1
-            u64 wold = 0;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (lane == v && have[v]) wold = atom_add_acquire(&wr[tgt[v]], kClaimWrite);
-            bool unp[V], emp[V];
-            u64 wslot[V];
-            u32 rd[V];
-            bool any_unp = false;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const u64 o = __shfl_sync(0xffffffffu, wold, v);
-                unp[v] = emp[v] = false;
-                wslot[v] = 0;
-                rd[v] = pk_readers(o);
-                if (have[v]) {
-                    const long long wt = pk_w(o), rt = pk_r(o);
-                    const u64 slot = (u64)delim[tgt[v]] + (u64)wt;
-                    if (!IPS4O_GUARD(ws.ctr, slot < delim[tgt[v] + 1], slot, delim[tgt[v] + 1])) {
+                } else {
+                    slot[v] = (u64)delim[tgt[v]] + (u64)w;
+                    if (!IPS4O_GUARD(ws.ctr, slot[v] < delim[tgt[v] + 1], slot[v], delim[tgt[v] + 1])) {
                         failed = true;
-                    } else if (wt <= rt) {
-                        if (IPS4O_GUARD(ws.ctr, slot < nbc, slot, nbc)) {
-                            unp[v] = true;
-                            any_unp = true;
-                        } else {
-                            failed = true;
-                        }
+                    } else if (w <= r) {
+                        if (IPS4O_GUARD(ws.ctr, slot[v] < nbc, slot[v], nbc)) ldt[v] = true;
+                        else failed = true;
                     } else {
                         emp[v] = true;
                     }
-                    wslot[v] = slot;
                 }
             }
             if (failed) break;
-            if (any_unp) {
+            // loads of all movers in flight together
 #pragma unroll
-                for (int v = 0; v < V; ++v)
-                    if (unp[v]) {
+            for (int v = 0; v < V; ++v) {
+                if (ldn[v] || ldt[v]) {
 #pragma unroll
-                        for (int q = 0; q < EPL; ++q) tmpb[v][q] = A[wslot[v] * B + lane + 32 * q];
-                    }
-                int mybk = 0;
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const K hk = __shfl_sync(0xffffffffu, T::key(tmpb[v][0]), 0);
-                    if (lane == v && unp[v]) mybk = classify_key<K>(hk, tree, spl, logL, eq);
+                    for (int q = 0; q < EPL; ++q) ldv[v][q] = A[slot[v] * B + lane + 32 * q];
                 }
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    const u32 t2 = (u32)__shfl_sync(0xffffffffu, mybk, v);
-                    if (unp[v]) {
-                        if (!IPS4O_GUARD(ws.ctr, t2 < nb, t2, nb)) {
-                            failed = true;
-                        } else if (t2 == tgt[v]) {
-                            ++skipped;                 // already in its bucket: leave it
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < EPL; ++q) {
-                                A[wslot[v] * B + lane + 32 * q] = buf[v][q];
-                                buf[v][q] = tmpb[v][q];
-                            }
-                            tgt[v] = t2;
-                            ++moved;
-                        }
-                    }
-                }
-                if (failed) break;
             }
+            // The warp barrier orders every lane's loads of the claimed blocks
+            // before the release that drops the reader count (release is
+            // cumulative): a writer that sees the count drained cannot
+            // overwrite a slot that is still being read.  The counts are
+            // dropped before this warp waits on any count itself, so two
+            // movers of one warp never wait on each other.
+            __syncwarp();
+#pragma unroll
+            for (int v = 0; v < V; ++v)
+                if (lane == v && ldn[v]) red_add_release64(&wr[prim[v]], kReadDone);
+            // writes into empty slots
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 if (!emp[v]) continue;
-                // empty slot: if a mover was reading from bucket t when the slot
-                // was claimed, wait until the count drains
+                // a mover was reading from bucket t when the slot was claimed:
+                // wait until the count drains
                 u32 ok = 1;
                 if (lane == v && rd[v] != 0) {
                     u32 it = 0;
                     while (pk_readers(ld_acquire64(&wr[tgt[v]])) != 0) {
                         if (++it > spin_limit) { ok = 0; break; }
-                        __nanosleep(64);
+                        __nanosleep(32);
                     }
                 }
                 ok = __shfl_sync(0xffffffffu, ok, v);
@@ -780,19 +691,84 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
                     failed = true;
                     break;
                 }
-                if (wslot[v] < nbc) {
+                if (slot[v] < nbc) {
 #pragma unroll
-                    for (int q = 0; q < EPL; ++q) A[wslot[v] * B + lane + 32 * q] = buf[v][q];
-                } else if (partial && wslot[v] == nbc) {
+                    for (int q = 0; q < EPL; ++q) A[slot[v] * B + lane + 32 * q] = hand[v][lane + 32 * q];
+                } else if (partial && slot[v] == nbc) {
 #pragma unroll
-                    for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = buf[v][q];
+                    for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = hand[v][lane + 32 * q];
                 } else {
-                    IPS4O_GUARD(ws.ctr, false, wslot[v], nbc);
+                    IPS4O_GUARD(ws.ctr, false, slot[v], nbc);
                     failed = true;
                     break;
                 }
                 have[v] = false;
                 ++moved;
+            }
+            if (failed) break;
+            // classify the first element of every block just loaded
+            int mybk = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const K hk = __shfl_sync(0xffffffffu, T::key(ldv[v][0]), 0);
+                if (lane == v && (ldn[v] || ldt[v])) mybk = classify_key<K>(hk, tree, spl, logL, eq);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const u32 t = (u32)__shfl_sync(0xffffffffu, mybk, v);
+                if (!(ldn[v] || ldt[v])) continue;
+                if (!IPS4O_GUARD(ws.ctr, t < nb, t, nb)) {
+                    failed = true;
+                    continue;
+                }
+                if (ldn[v]) {
+#pragma unroll
+                    for (int q = 0; q < EPL; ++q) hand[v][lane + 32 * q] = ldv[v][q];
+                    have[v] = true;
+                    tgt[v] = t;
+                } else if (t == tgt[v]) {
+                    ++skipped;                     // already in its bucket: leave it
+                } else {
+                    // swap: the carried block goes to slot w_t, the block found
+                    // there is carried on (each lane touches only its elements)
+#pragma unroll
+                    for (int q = 0; q < EPL; ++q) {
+                        A[slot[v] * B + lane + 32 * q] = hand[v][lane + 32 * q];
+                        hand[v][lane + 32 * q] = ldv[v][q];
+                    }
+                    tgt[v] = t;
+                    ++moved;
+                }
+            }
+            if (failed) break;
+            if (any_exd) {
+                // movers whose primary bucket ran dry pick the next live one
+                __syncwarp();
+                if (lane < 8) exw = ld_relaxed(&exh[lane]);
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    if (!exd[v]) continue;
+                    const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
+                    // lane l < 8 looks at word (pw + l) % 8; lane 8 at the bits of
+                    // word pw before prim (the end of the cycle)
+                    const u32 word_l = __shfl_sync(0xffffffffu, exw, (pw + (u32)lane) & 7u);
+                    const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
+                    u32 free_bits = 0u;
+                    if (lane < 8) free_bits = ~word_l;
+                    if (lane == 0) free_bits &= ~((1u << pb) - 1u);
+                    if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
+                    const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
+                    if (ball == 0) {
+                        done[v] = true;
+                        continue;
+                    }
+                    const int first = __ffs(ball) - 1;
+                    const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
+                    const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
+                    const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
+                    if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
+                    else { failed = true; done[v] = true; }
+                }
             }
         }
     }
@@ -806,22 +782,17 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB)
 template <class T>
 struct CleanupCfg {
     typedef typename T::elem_t E;
-    static constexpr int TPB = BaseCfg<T>::TPB;
+    static constexpr int TPB = 256;
     static constexpr int B = T::kBlock;
-    // the cleanup arrays and the base-case arrays share the dynamic shared
-    // memory: the base case starts only after the cleanup copy is complete
     static constexpr size_t off_ov = 0;
     static constexpr size_t off_lpre = off_ov + (size_t)B * sizeof(E);
     static constexpr size_t off_src = off_lpre + (size_t)(kMaxStripesPerSub + 1) * 4 + 4;
-    static constexpr size_t cleanup_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
-    static constexpr size_t smem_bytes =
-        cleanup_bytes > BaseCfg<T>::smem_bytes ? cleanup_bytes : BaseCfg<T>::smem_bytes;
+    static constexpr size_t smem_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
 };
 
 template <class T>
-__global__ void __launch_bounds__(CleanupCfg<T>::TPB, 2)
-    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 base_cap, u32 spin_limit, u32 partition_only,
-              u64 seed) {
+__global__ void __launch_bounds__(CleanupCfg<T>::TPB)
+    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit, u32 partition_only, u32 rec_cap) {
     typedef typename T::elem_t E;
     typedef CleanupCfg<T> C;
     constexpr int TPB = C::TPB, B = C::B;
@@ -931,13 +902,21 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB, 2)
     const u64 size = Eb - Bb;
     const bool is_eq = sub.eq && (b & 1);
     if (is_eq || size < 2) return;
-    if (size <= base_cap) {
-        cta_sort<T>(A + Bb, (u32)size, smem_raw, seed ^ mix64(sub.begin + Bb));
-        if (threadIdx.x == 0) atomicAdd(&ws.ctr->base_buckets, 1ull);
-    } else if (threadIdx.x == 0) {
-        u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
-        if (idx < ws.next_cap) ws.next_tasks[idx] = Task{sub.begin + Bb, size};
-        else set_status(ws.ctr, kStatusCapacity);
+    if (threadIdx.x == 0) {
+        // buckets up to the base-case capacity are sorted in shared memory by
+        // the base-case kernels that follow; larger ones recurse (Section 4)
+        const Task task{sub.begin + Bb, size};
+        if (size > (u64)rec_cap) {
+            const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
+            if (idx < ws.next_cap) ws.next_tasks[idx] = task;
+            else set_status(ws.ctr, kStatusCapacity);
+        } else if (size <= (u64)T::kBaseSmall) {
+            const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
+            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
+        } else {
+            const u32 idx = atomicAdd(&ws.ctr->base_large, 1u);
+            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_large[idx] = task;
+        }
     }
 }
 

@@ -58,5 +58,5 @@ def test_params_validation(lib):
 
 def test_base_case_capacity(lib):
     from paper_1705_02257_gb300 import ips4o
-    assert ips4o.ips4o_base_case_capacity(ips4o.U64) == 8192
-    assert ips4o.ips4o_base_case_capacity(ips4o.PAIR_U64) == 4096
+    assert ips4o.ips4o_base_case_capacity(ips4o.U64) == 16384
+    assert ips4o.ips4o_base_case_capacity(ips4o.PAIR_U64) == 8192

@@ -182,3 +182,18 @@ def test_sort_host_roundtrip(ips4o):
     b = a.copy()
     ips4o.sort_host(b, "u64")
     assert np.array_equal(b, oracle.sort(a, "u64"))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "two_dup", "exponential", "ones"])
+@pytest.mark.parametrize("k_max,bcm", [(256, 64), (4, 256), (16, 100)])
+def test_deep_recursion(ips4o, dist, k_max, bcm):
+    """A small base case and few buckets force several distribution levels
+    (Section 4: the step recurses on every non-equality bucket)."""
+    ips4o.set_params(base_case_max=bcm, k_max=k_max)
+    try:
+        a = inputs.u64(200_003, dist)
+        check_u64(ips4o, a)
+        if dist in ("uniform", "exponential"):
+            assert ips4o.stats()["levels"] >= 2
+    finally:
+        ips4o.reset_params()
