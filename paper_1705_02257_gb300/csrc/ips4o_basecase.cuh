@@ -152,10 +152,10 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 // Sort g[0..m), m <= CAP, with the whole CTA (BaseCfg<T>::TPB threads).
 //
 // The bucket is read once into registers.  Its key range [lo, hi] is split
-// into KB equal sub-ranges, KB about m / 4, and every element goes to
-// sub-bucket floor((key - lo) * KB / (hi - lo + 1)) (one 64-bit
-// multiply-high); a bucket produced by the sampled distribution steps is
-// close to uniform over its range, so the sub-buckets are small.  After a
+// into at most KB (about m / 4) sub-ranges of equal power-of-two width, and
+// every element goes to sub-bucket (key - lo) >> shift; a bucket produced by
+// the sampled distribution steps is close to uniform over its range, so the
+// sub-buckets are small.  After a
 // counting-sort scatter into shared memory, each element's final position is
 // the start of its sub-bucket plus the number of keys of that sub-bucket
 // that are smaller (or equal and earlier), and it is written there directly.
@@ -209,15 +209,16 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     if (all_equal) return;                         // all keys equal: already sorted (uniform exit)
     u32 KB = pow2_ceil_u32((m + C::N0 - 1) / C::N0);
     KB = KB < 2 ? 2 : (KB > (u32)C::MAXSUB ? (u32)C::MAXSUB : KB);
+    // sub-bucket = (key - lo) >> shift, with shift chosen so that the whole
+    // range [lo, hi] maps into [0, KB): a monotone map of the key, so lower
+    // sub-buckets hold smaller keys; sub-buckets cover equal key ranges
     const u64 range = (u64)(hi - lo);             // >= 1
-    const bool direct = range < KB;               // few distinct values: one sub-bucket per value
-    // floor(2^64 / (range + 1)) * KB, without dividing by zero when the
-    // bucket spans the whole 64-bit key range
-    const u64 mult = direct ? 0 : (range == ~0ull ? (u64)KB : (~0ull / (range + 1)) * KB);
+    const int bits = 64 - __clzll((long long)range);
+    const int logkb = 31 - __clz(KB);
+    const int shift = bits > logkb ? bits - logkb : 0;
     auto sub_of = [&](const K& k) -> u32 {
-        const u64 d = (u64)(k - lo);
-        const u32 b = direct ? (u32)d : (u32)__umul64hi(d, mult);
-        return b < KB ? b : KB - 1;
+        const u64 d = (u64)(k - lo) >> shift;
+        return d < (u64)KB ? (u32)d : KB - 1;
     };
     u32 rk2[EPT / 2];
 #pragma unroll

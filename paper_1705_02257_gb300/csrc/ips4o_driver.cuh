@@ -197,8 +197,11 @@ struct Driver {
                                         (int)BaseSmall<T>::smem_bytes));
         IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)BaseLarge<T>::smem_bytes));
+        IPS4O_CUDA(cudaFuncSetAttribute(k_permute<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)PermuteCfg<T>::smem_bytes));
         int occ = 0;
-        IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB, 0));
+        IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB,
+                                                                 PermuteCfg<T>::smem_bytes));
         permute_grid = std::max(1, occ) * st.sms;
         st.stats = ips4o_stats{};
         st.stats.workspace_bytes = st.ws_bytes;
@@ -356,7 +359,8 @@ struct Driver {
         IPS4O_LAUNCH(1, (k_classify<T><<<cgrid, ClassifyCfg<T>::TPB, ClassifyCfg<T>::smem_bytes, stream>>>(d, ws, nstr)));
         IPS4O_LAUNCH(2, (k_prefix<T, 256><<<nsub, 256, 0, stream>>>(ws, nsub)));
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
-        IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, 0, stream>>>(d, ws, nsub, kSpinLimit)));
+        IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
+                            d, ws, nsub, kSpinLimit)));
         IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * kMaxBuckets, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
                             d, ws, nsub, kSpinLimit, partition ? 1u : 0u, rec_cap)));
         if (!partition) {

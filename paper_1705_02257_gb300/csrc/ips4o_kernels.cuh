@@ -479,43 +479,51 @@ __global__ void __launch_bounds__(TPB) k_fix(typename T::elem_t* arr, Workspace<
 // waits (boundedly) until the count it observed has drained.  Buckets found
 // empty are recorded in a bitmap so that movers stop probing them.
 //
-// Each warp runs V movers in lockstep: their pointer atomics, block loads
-// and block stores are issued by the same instructions, so one warp keeps
-// V blocks in flight.
+// Lane v < V of a warp is mover v: its pointer claims, decisions, the
+// classification of block heads and the search for a new primary bucket run
+// in parallel across the lanes.  Blocks are moved by the whole warp, one
+// coalesced 512-byte copy per block (cp.async into the mover's two
+// shared-memory block buffers; stores from shared memory), so one warp keeps
+// up to V blocks in flight.
 template <class T>
 struct PermuteCfg {
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
     static constexpr int TPB = 256;
     static constexpr int NW = TPB / 32;
-    static constexpr int V = 8;                  // movers per warp
-    static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block
+    static constexpr int V = 16;                 // movers per warp (lanes 0..V-1)
+    static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block copy
     static constexpr int MAX_MOVERS_PER_BUCKET = 64;
+    static constexpr size_t off_buf = 0;                                          // E[NW][2][V][B]
+    static constexpr size_t off_tree = off_buf + (size_t)NW * 2 * V * T::kBlock * sizeof(E);
+    static constexpr size_t off_spl = off_tree + (size_t)NW * kMaxLeaves * sizeof(K);
+    static constexpr size_t off_delim = off_spl + (size_t)NW * kMaxLeaves * sizeof(K);
+    static constexpr size_t off_gpre = off_delim + (size_t)NW * (kMaxBuckets + 1) * 4;
+    static constexpr size_t smem_bytes = off_gpre + 1025 * 4 + 64 * 8;
     static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
 };
 
 template <class T>
-__global__ void __launch_bounds__(PermuteCfg<T>::TPB, 2)
+__global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
     k_permute(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
     constexpr int TPB = C::TPB, NW = C::NW, V = C::V, EPL = C::EPL, B = T::kBlock;
-    __shared__ u32 s_gpre[1025];
-    __shared__ u64 s_tot;
-    __shared__ u32 tmp[32];
-    __shared__ K s_tree[NW][kMaxLeaves];
-    __shared__ K s_spl[NW][kMaxLeaves];
-    __shared__ u32 s_delim[NW][kMaxBuckets + 1];
-    __shared__ E s_hand[NW][V][B];               // the block each mover carries
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    u32* s_gpre = (u32*)(smem_raw + C::off_gpre);
+    u64* s_misc = (u64*)(smem_raw + C::off_gpre + 1025 * 4 + 4);   // [0] total, [1..33] scan tmp
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool is_mover = lane < V;
     const u32 G = gridDim.x * NW;                 // warps in the grid
     // mover groups (warps) per subproblem, in proportion to its full blocks
     u64 mine = 0;
     for (u32 i = threadIdx.x; i < nsub; i += TPB) mine += ws.subs[i].blocks_total;
-    if (threadIdx.x == 0) s_tot = 0;
+    if (threadIdx.x == 0) s_misc[0] = 0;
     __syncthreads();
-    atomicAdd(&s_tot, mine);
+    atomicAdd(&s_misc[0], mine);
     __syncthreads();
-    const u64 total = s_tot;
+    const u64 total = s_misc[0];
     {
         constexpr int PER = 1024 / TPB;
         u32 gv[PER], sum = 0;
@@ -540,7 +548,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 2)
             sum += gv[q];
         }
         u32 tot;
-        u32 p = block_exclusive_scan<u32>(sum, tmp, &tot);
+        u32 p = block_exclusive_scan<u32>(sum, (u32*)(s_misc + 1), &tot);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const u32 i = threadIdx.x * PER + q;
@@ -551,9 +559,10 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 2)
         __syncthreads();
     }
     const u32 GT = s_gpre[nsub];
-    K* tree = s_tree[warp];
-    K* spl = s_spl[warp];
-    u32* delim = s_delim[warp];
+    E* wbuf = (E*)(smem_raw + C::off_buf) + (size_t)warp * 2 * V * B;   // [2][V][B]
+    K* tree = (K*)(smem_raw + C::off_tree) + (size_t)warp * kMaxLeaves;
+    K* spl = (K*)(smem_raw + C::off_spl) + (size_t)warp * kMaxLeaves;
+    u32* delim = (u32*)(smem_raw + C::off_delim) + (size_t)warp * (kMaxBuckets + 1);
     u64 moved = 0, skipped = 0;
     bool failed = false;
     for (u32 g = blockIdx.x * NW + warp; g < GT && !failed; g += G) {
@@ -581,201 +590,146 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 2)
         const u64 nbc = sub.n / B;                   // complete block slots
         const bool partial = (sub.n % B) != 0;
 
-        // per-mover state (arrays indexed by compile-time v only); the block a
-        // mover carries lives in shared memory, only freshly loaded blocks in
-        // registers
-        E (*hand)[B] = s_hand[warp];
-        E ldv[V][EPL];
-        u32 prim[V], tgt[V];
-        bool have[V], done[V];
+        // per-lane mover state (lanes >= V never become active)
+        u32 prim = is_mover ? (u32)(((u64)(gl * V + lane) * nb) / nmov) : 0u;
+        u32 tgt = 0, hand = 0;                     // hand: which of the two buffers holds the carried block
+        bool have = false, done = !is_mover;
+        u32 exw[8];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            prim[v] = (u32)(((u64)(gl * V + v) * nb) / nmov);
-            tgt[v] = 0;
-            have[v] = false;
-            done[v] = false;
-        }
-        // lanes 0..7 hold one word each of the exhausted-bucket bitmap
-        u32 exw = lane < 8 ? ld_relaxed(&exh[lane]) : 0xffffffffu;
-        // One step per mover and iteration: a mover with empty hands claims a
-        // block of its primary bucket (readers + 1, r_p - 1) and loads it; a
-        // mover holding a block claims slot w_t of its destination and loads
-        // the block found there if it is unprocessed.  So every iteration costs
-        // one atomic and one load round trip for all V movers together.
+        for (int w8 = 0; w8 < 8; ++w8) exw[w8] = 0;
+        bool exw_valid = false;
         for (;;) {
-            bool any_active = false;
-#pragma unroll
-            for (int v = 0; v < V; ++v) any_active |= !done[v];
-            if (!any_active || failed) break;
+            if (!__any_sync(0xffffffffu, !done) || failed) break;
+            // ---- one claim per active mover
             u64 old = 0;
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (lane == v && !done[v]) {
-                    if (have[v]) old = atom_add_acquire(&wr[tgt[v]], kClaimWrite);
-                    else old = atomicAdd(&wr[prim[v]], kClaimRead);
-                }
-            bool ldn[V], ldt[V], emp[V], exd[V];
-            u64 slot[V];
-            u32 rd[V];
-            bool any_exd = false;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const u64 o = __shfl_sync(0xffffffffu, old, v);
-                ldn[v] = ldt[v] = emp[v] = exd[v] = false;
-                slot[v] = 0;
-                rd[v] = pk_readers(o);
-                if (done[v]) continue;
-                const long long w = pk_w(o), r = pk_r(o);
-                if (!have[v]) {
+            if (!done) {
+                if (have) old = atom_add_acquire(&wr[tgt], kClaimWrite);
+                else old = atomicAdd(&wr[prim], kClaimRead);
+            }
+            const long long w = pk_w(old), r = pk_r(old);
+            const u32 rd = pk_readers(old);
+            bool ldn = false, ldt = false, emp = false, exd = false;
+            u64 slot = 0;
+            if (!done) {
+                if (!have) {
                     if (r < w) {
-                        // no unprocessed block left in the primary bucket
-                        if (lane == v) {
-                            red_add_relaxed64(&wr[prim[v]], kReadDone);
-                            atomicOr(&exh[prim[v] >> 5], 1u << (prim[v] & 31));
-                        }
-                        exd[v] = true;
-                        any_exd = true;
+                        // no unprocessed block left in the primary bucket: undo
+                        red_add_relaxed64(&wr[prim], kReadDone);
+                        atomicOr(&exh[prim >> 5], 1u << (prim & 31));
+                        exd = true;
                     } else {
-                        slot[v] = (u64)delim[prim[v]] + (u64)r;
-                        if (IPS4O_GUARD(ws.ctr, r >= 0 && slot[v] < nbc, slot[v], nbc)) ldn[v] = true;
+                        slot = (u64)delim[prim] + (u64)r;
+                        if (IPS4O_GUARD(ws.ctr, r >= 0 && slot < nbc, slot, nbc)) ldn = true;
                         else failed = true;
                     }
                 } else {
-                    slot[v] = (u64)delim[tgt[v]] + (u64)w;
-                    if (!IPS4O_GUARD(ws.ctr, slot[v] < delim[tgt[v] + 1], slot[v], delim[tgt[v] + 1])) {
+                    slot = (u64)delim[tgt] + (u64)w;
+                    if (!IPS4O_GUARD(ws.ctr, slot < delim[tgt + 1], slot, delim[tgt + 1])) {
                         failed = true;
                     } else if (w <= r) {
-                        if (IPS4O_GUARD(ws.ctr, slot[v] < nbc, slot[v], nbc)) ldt[v] = true;
+                        if (IPS4O_GUARD(ws.ctr, slot < nbc, slot, nbc)) ldt = true;
                         else failed = true;
                     } else {
-                        emp[v] = true;
+                        emp = true;
                     }
                 }
             }
-            if (failed) break;
-            // loads of all movers in flight together
+            if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
+            // ---- block loads of all movers, one coalesced copy per block
+            {
+                unsigned m = __ballot_sync(0xffffffffu, ldn || ldt);
+                while (m) {
+                    const int v = __ffs(m) - 1;
+                    m &= m - 1;
+                    const u64 sv = __shfl_sync(0xffffffffu, slot, v);
+                    const u32 hb = __shfl_sync(0xffffffffu, hand, v) ^ 1u;      // the free buffer
+                    E* dst = wbuf + ((size_t)hb * V + v) * B;
+                    const E* src = A + sv * B;
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (ldn[v] || ldt[v]) {
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) ldv[v][q] = A[slot[v] * B + lane + 32 * q];
+                    for (int q = 0; q < EPL; ++q) cp_async<sizeof(E)>(dst + lane + 32 * q, src + lane + 32 * q);
                 }
-            }
-            // The warp barrier orders every lane's loads of the claimed blocks
-            // before the release that drops the reader count (release is
-            // cumulative): a writer that sees the count drained cannot
-            // overwrite a slot that is still being read.  The counts are
-            // dropped before this warp waits on any count itself, so two
-            // movers of one warp never wait on each other.
-            __syncwarp();
-#pragma unroll
-            for (int v = 0; v < V; ++v)
-                if (lane == v && ldn[v]) red_add_release64(&wr[prim[v]], kReadDone);
-            // writes into empty slots
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                if (!emp[v]) continue;
-                // a mover was reading from bucket t when the slot was claimed:
-                // wait until the count drains
-                u32 ok = 1;
-                if (lane == v && rd[v] != 0) {
-                    u32 it = 0;
-                    while (pk_readers(ld_acquire64(&wr[tgt[v]])) != 0) {
-                        if (++it > spin_limit) { ok = 0; break; }
-                        __nanosleep(32);
-                    }
-                }
-                ok = __shfl_sync(0xffffffffu, ok, v);
-                if (!ok) {
-                    if (lane == 0) set_status(ws.ctr, kStatusTimeout);
-                    failed = true;
-                    break;
-                }
-                if (slot[v] < nbc) {
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) A[slot[v] * B + lane + 32 * q] = hand[v][lane + 32 * q];
-                } else if (partial && slot[v] == nbc) {
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) ovf[lane + 32 * q] = hand[v][lane + 32 * q];
-                } else {
-                    IPS4O_GUARD(ws.ctr, false, slot[v], nbc);
-                    failed = true;
-                    break;
-                }
-                have[v] = false;
-                ++moved;
-            }
-            if (failed) break;
-            // classify the first element of every block just loaded
-            int mybk = 0;
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const K hk = __shfl_sync(0xffffffffu, T::key(ldv[v][0]), 0);
-                if (lane == v && (ldn[v] || ldt[v])) mybk = classify_key<K>(hk, tree, spl, logL, eq);
-            }
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const u32 t = (u32)__shfl_sync(0xffffffffu, mybk, v);
-                if (!(ldn[v] || ldt[v])) continue;
-                if (!IPS4O_GUARD(ws.ctr, t < nb, t, nb)) {
-                    failed = true;
-                    continue;
-                }
-                if (ldn[v]) {
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) hand[v][lane + 32 * q] = ldv[v][q];
-                    have[v] = true;
-                    tgt[v] = t;
-                } else if (t == tgt[v]) {
-                    ++skipped;                     // already in its bucket: leave it
-                } else {
-                    // swap: the carried block goes to slot w_t, the block found
-                    // there is carried on (each lane touches only its elements)
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) {
-                        A[slot[v] * B + lane + 32 * q] = hand[v][lane + 32 * q];
-                        hand[v][lane + 32 * q] = ldv[v][q];
-                    }
-                    tgt[v] = t;
-                    ++moved;
-                }
-            }
-            if (failed) break;
-            if (any_exd) {
-                // movers whose primary bucket ran dry pick the next live one
+                cp_async_commit();
+                cp_async_wait<0>();
                 __syncwarp();
-                if (lane < 8) exw = ld_relaxed(&exh[lane]);
-#pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    if (!exd[v]) continue;
-                    const u32 pw = prim[v] >> 5, pb = prim[v] & 31;
-                    // lane l < 8 looks at word (pw + l) % 8; lane 8 at the bits of
-                    // word pw before prim (the end of the cycle)
-                    const u32 word_l = __shfl_sync(0xffffffffu, exw, (pw + (u32)lane) & 7u);
-                    const u32 wrapw = __shfl_sync(0xffffffffu, exw, pw);
-                    u32 free_bits = 0u;
-                    if (lane < 8) free_bits = ~word_l;
-                    if (lane == 0) free_bits &= ~((1u << pb) - 1u);
-                    if (lane == 8) free_bits = ~wrapw & ((1u << pb) - 1u);
-                    const u32 ball = __ballot_sync(0xffffffffu, free_bits != 0);
-                    if (ball == 0) {
-                        done[v] = true;
-                        continue;
-                    }
-                    const int first = __ffs(ball) - 1;
-                    const u32 fb = __shfl_sync(0xffffffffu, free_bits, first);
-                    const u32 word = first == 8 ? pw : ((pw + (u32)first) & 7u);
-                    const u32 np = word * 32 + (u32)(__ffs(fb) - 1);
-                    if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim[v] = np;
-                    else { failed = true; done[v] = true; }
+            }
+            // The warp barrier orders every lane's copies of the claimed blocks
+            // before the release that drops the reader count (release is
+            // cumulative): a writer that sees the count drained cannot overwrite
+            // a slot that is still being read.  Counts are dropped before this
+            // warp waits on any count, so movers of one warp never wait on each
+            // other.
+            if (ldn) red_add_release64(&wr[prim], kReadDone);
+            // ---- writes into empty slots (after the reader counts drained)
+            bool ok = true;
+            if (emp && rd != 0) {
+                u32 it = 0;
+                while (pk_readers(ld_acquire64(&wr[tgt])) != 0) {
+                    if (++it > spin_limit) { ok = false; break; }
+                    __nanosleep(32);
                 }
             }
+            if (!ok) set_status(ws.ctr, kStatusTimeout);
+            if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
+            bool bad_slot = emp && !(slot < nbc || (partial && slot == nbc));
+            if (bad_slot) IPS4O_GUARD(ws.ctr, false, slot, nbc);
+            if (__any_sync(0xffffffffu, bad_slot)) { failed = true; break; }
+            // ---- classify the head of every block just loaded
+            int t = 0;
+            if (ldn || ldt) {
+                const E* blk = wbuf + ((size_t)(hand ^ 1u) * V + lane) * B;
+                t = classify_key<K>(T::key(blk[0]), tree, spl, logL, eq);
+                if (!IPS4O_GUARD(ws.ctr, t >= 0 && (u32)t < nb, t, nb)) failed = true;
+            }
+            if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
+            const bool swp = ldt && (u32)t != tgt;           // the slot's block must move on
+            if (ldt && !swp) ++skipped;                       // already in its bucket: leave it
+            // ---- stores: carried blocks into empty slots and swap slots
+            {
+                unsigned m = __ballot_sync(0xffffffffu, emp || swp);
+                while (m) {
+                    const int v = __ffs(m) - 1;
+                    m &= m - 1;
+                    const u64 sv = __shfl_sync(0xffffffffu, slot, v);
+                    const u32 hb = __shfl_sync(0xffffffffu, hand, v);
+                    const E* src = wbuf + ((size_t)hb * V + v) * B;
+                    E* dst = sv < nbc ? A + sv * B : ovf;
+#pragma unroll
+                    for (int q = 0; q < EPL; ++q) dst[lane + 32 * q] = src[lane + 32 * q];
+                }
+                __syncwarp();
+            }
+            if (emp) { have = false; ++moved; }
+            if (swp) { hand ^= 1u; tgt = (u32)t; ++moved; }
+            if (ldn) { hand ^= 1u; tgt = (u32)t; have = true; }
+            // ---- movers whose primary bucket ran dry pick the next live one
+            if (__any_sync(0xffffffffu, exd)) {
+                if (exd) {
+#pragma unroll
+                    for (int w8 = 0; w8 < 8; ++w8) exw[w8] = ld_relaxed(&exh[w8]);
+                    exw_valid = true;
+                    // first non-exhausted bucket after prim, cyclically
+                    u32 np = 0xffffffffu;
+                    for (u32 step = 1; step <= 8 * 32 && np == 0xffffffffu; ) {
+                        const u32 c = (prim + step) & 255u;
+                        const u32 free_bits = ~exw[c >> 5] >> (c & 31);
+                        if (free_bits) {
+                            const u32 cand = c + (u32)(__ffs(free_bits) - 1);
+                            // a candidate past the end of this word wraps at bit 31
+                            np = cand;
+                        } else {
+                            step += 32 - (c & 31);
+                        }
+                    }
+                    if (np == 0xffffffffu) done = true;
+                    else if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim = np;
+                    else { failed = true; done = true; }
+                }
+            }
+            (void)exw_valid;
         }
     }
-    if (lane == 0) {
-        if (moved) atomicAdd(&ws.ctr->blocks_moved, moved);
-        if (skipped) atomicAdd(&ws.ctr->blocks_skipped, skipped);
-    }
+    if (moved) atomicAdd(&ws.ctr->blocks_moved, moved);
+    if (skipped) atomicAdd(&ws.ctr->blocks_skipped, skipped);
 }
 
 // --------------------------------------------------------------- cleanup
