@@ -95,7 +95,7 @@ struct BaseCfg {
     static constexpr int NW = TPB / 32;
     static constexpr int CAP = CAP_;
     static constexpr int EPT = CAP / TPB;
-    static constexpr int N0 = 4;             // target sub-bucket size
+    static constexpr int N0 = 2;             // target sub-bucket size
     static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
     static constexpr int LIMIT = 64;         // any larger sub-bucket: whole-bucket bitonic fallback
     static constexpr size_t off_data = 0;

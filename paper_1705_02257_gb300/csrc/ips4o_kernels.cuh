@@ -94,32 +94,48 @@ struct ClassifyCfg {
     static constexpr size_t off_bscan = off_off + kMaxBuckets * 4;
     static constexpr size_t off_total = off_bscan + kMaxBuckets * 4;
     static constexpr size_t off_blkb = off_total + kMaxBuckets * 4;
-    static constexpr size_t off_misc = off_blkb + MAXBLK * 2;
+    static constexpr size_t off_emit = off_blkb + MAXBLK * 2;
+    static constexpr size_t off_misc = off_emit + kMaxBuckets * 2;
     static constexpr size_t smem_bytes = off_misc + 64 * 8;
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
+    static_assert(MAXBLK < 65536 && TILE < (1 << 30), "packed scan fields");
     static_assert(TILE % TPB == 0, "tile must be a multiple of the CTA size");
 };
 
 // Bucket ids of IPT keys, descending the tree level by level for all keys at
-// once so that the IPT independent shared-memory lookups overlap.
-template <class K, int IPT>
-__device__ __forceinline__ void classify_many(const K (&k)[IPT], const bool (&valid)[IPT], const K* tree,
-                                              const K* spl, int logL, bool eq, int (&bk)[IPT]) {
+// once so that the IPT independent shared-memory lookups overlap.  LOGL is
+// the tree depth (log2 of the number of leaves), fixed at compile time.
+template <class K, int IPT, int LOGL>
+__device__ __forceinline__ void classify_fixed(const K (&k)[IPT], const K* tree, const K* spl, bool eq,
+                                               int (&bk)[IPT]) {
     int j[IPT];
 #pragma unroll
     for (int q = 0; q < IPT; ++q) j[q] = 1;
 #pragma unroll
-    for (int l = 0; l < 8; ++l) {
-        if (l < logL) {
+    for (int l = 0; l < LOGL; ++l) {
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) j[q] = 2 * j[q] + (tree[j[q]] <= k[q] ? 1 : 0);
-        }
+        for (int q = 0; q < IPT; ++q) j[q] = 2 * j[q] + (tree[j[q]] <= k[q] ? 1 : 0);
     }
 #pragma unroll
     for (int q = 0; q < IPT; ++q) {
-        int i = j[q] - (1 << logL);
+        int i = j[q] - (1 << LOGL);
         if (eq) i = 2 * i - ((i > 0 && spl[i] == k[q]) ? 1 : 0);
-        bk[q] = valid[q] ? i : -1;
+        bk[q] = i;
+    }
+}
+
+template <class K, int IPT>
+__device__ __forceinline__ void classify_many(const K (&k)[IPT], const K* tree, const K* spl, int logL, bool eq,
+                                              int (&bk)[IPT]) {
+    switch (logL) {
+    case 8: classify_fixed<K, IPT, 8>(k, tree, spl, eq, bk); break;
+    case 7: classify_fixed<K, IPT, 7>(k, tree, spl, eq, bk); break;
+    case 6: classify_fixed<K, IPT, 6>(k, tree, spl, eq, bk); break;
+    case 5: classify_fixed<K, IPT, 5>(k, tree, spl, eq, bk); break;
+    case 4: classify_fixed<K, IPT, 4>(k, tree, spl, eq, bk); break;
+    case 3: classify_fixed<K, IPT, 3>(k, tree, spl, eq, bk); break;
+    case 2: classify_fixed<K, IPT, 2>(k, tree, spl, eq, bk); break;
+    default: classify_fixed<K, IPT, 1>(k, tree, spl, eq, bk); break;
     }
 }
 
@@ -137,10 +153,11 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
     K* s_spl = (K*)(smem_raw + C::off_spl);
     u32* s_fill = (u32*)(smem_raw + C::off_fill);
     u32* s_cnt = (u32*)(smem_raw + C::off_cnt);
-    u32* s_off = (u32*)(smem_raw + C::off_off);
+    u32* s_off = (u32*)(smem_raw + C::off_off);     // grouped-tile offset of a bucket that fills a block
     u32* s_bscan = (u32*)(smem_raw + C::off_bscan);
     u32* s_total = (u32*)(smem_raw + C::off_total);
     unsigned short* s_blkb = (unsigned short*)(smem_raw + C::off_blkb);
+    unsigned short* s_emit = (unsigned short*)(smem_raw + C::off_emit);   // buckets emitting in this tile
     u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp, [40] stripe id
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -159,17 +176,17 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
         }
         for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
         E* A = arr + sd.begin;
-        const u64 len = sd.end - sd.begin;
-        const u32 ntiles = (u32)ceil_div(len, TILE);
+        const u32 len = (u32)(sd.end - sd.begin);   // a stripe holds < 2^32 elements
+        const u32 ntiles = (len + TILE - 1) / TILE;
         u32 front = 0;                       // full blocks written at the stripe front
         __syncthreads();
 
         auto issue = [&](u32 tn) {
             E* dst = stage + (tn % STAGES) * TILE;
-            const u64 tb = (u64)tn * TILE;
+            const u32 tb = tn * TILE;
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
-                u32 idx = tid + q * TPB;
+                const u32 idx = tid + q * TPB;
                 if (tb + idx < len) cp_async<sizeof(E)>(dst + idx, A + tb + idx);
             }
         };
@@ -184,23 +201,22 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
             cp_async_wait<STAGES - 1>();
             __syncthreads();
             E* tile = stage + (t % STAGES) * TILE;
-            const u64 tb = (u64)t * TILE;
-            const u32 tcount = (u32)((len - tb) < (u64)TILE ? (len - tb) : (u64)TILE);
+            const u32 tb = t * TILE;
+            const u32 tcount = len - tb < (u32)TILE ? len - tb : (u32)TILE;
             E e[IPT];
             K k[IPT];
-            bool valid[IPT];
             int bk[IPT];
             u32 rk[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 const u32 idx = tid + q * TPB;
-                valid[q] = idx < tcount;
-                e[q] = tile[valid[q] ? idx : 0];
+                e[q] = tile[idx < tcount ? idx : 0];
                 k[q] = T::key(e[q]);
             }
-            classify_many<K, IPT>(k, valid, s_tree, s_spl, logL, eq, bk);
+            classify_many<K, IPT>(k, s_tree, s_spl, logL, eq, bk);
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
+                if (tid + q * TPB >= tcount) bk[q] = -1;
                 // rank within the tile's run of the bucket; a warp whose lanes
                 // all hit one bucket (long runs, repeated keys) takes one atomic
                 const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
@@ -213,26 +229,39 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
                 }
             }
             __syncthreads();
-            // per-bucket run offsets in the tile and full blocks to emit
+            // Buckets whose buffer block fills in this tile emit full blocks;
+            // their new elements are grouped in the (now free) staging slot.
+            // The new elements of every other bucket go straight into its
+            // buffer block.
             u32 c = 0, f = 0, nfull = 0;
             if (tid < kMaxBuckets) {
                 c = s_cnt[tid];
                 f = s_fill[tid];
                 nfull = (f + c) / B;
             }
+            // one scan of three packed counts: [tile offset 32 | blocks 16 | emitting buckets 16]
             u64 tot;
-            const u64 pre = block_exclusive_scan<u64>(((u64)c << 32) | nfull, s_misc, &tot);
-            const u32 tot_blocks = (u32)(tot & 0xffffffffu);
+            const u64 pre = block_exclusive_scan<u64>(((u64)(nfull ? c : 0u) << 32) | ((u64)nfull << 16) |
+                                                          (nfull ? 1u : 0u),
+                                                      s_misc, &tot);
+            const u32 tot_blocks = (u32)((tot >> 16) & 0xffffu);
+            const u32 n_emit = (u32)(tot & 0xffffu);
             if (tid < kMaxBuckets) {
-                s_off[tid] = (u32)(pre >> 32);
-                s_bscan[tid] = (u32)(pre & 0xffffffffu);
-                for (u32 q = 0; q < nfull; ++q) s_blkb[(u32)(pre & 0xffffffffu) + q] = (unsigned short)tid;
+                const u32 bpre = (u32)((pre >> 16) & 0xffffu);
+                s_off[tid] = nfull ? (u32)(pre >> 32) : 0xffffffffu;
+                s_bscan[tid] = bpre;
+                for (u32 q = 0; q < nfull; ++q) s_blkb[bpre + q] = (unsigned short)tid;
+                if (nfull) s_emit[(u32)(pre & 0xffffu)] = (unsigned short)tid;
             }
             __syncthreads();
-            // group the tile by bucket (the staging slot is free now)
 #pragma unroll
-            for (int q = 0; q < IPT; ++q)
-                if (bk[q] >= 0) tile[s_off[bk[q]] + rk[q]] = e[q];
+            for (int q = 0; q < IPT; ++q) {
+                if (bk[q] >= 0) {
+                    const u32 ob = s_off[bk[q]];
+                    if (ob == 0xffffffffu) buf[bk[q] * B + s_fill[bk[q]] + rk[q]] = e[q];
+                    else tile[ob + rk[q]] = e[q];
+                }
+            }
             __syncthreads();
             // write full blocks over the front of the stripe
             for (u32 i = warp; i < tot_blocks; i += NW) {
@@ -240,28 +269,27 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
                 const u32 jb = i - s_bscan[b];
                 const u32 fb = s_fill[b];
                 const u32 ob = s_off[b];
-                const u64 dst = (u64)(front + i) * B;
+                const u32 dst = (front + i) * B;
                 if (dst + B <= len) {
+                    E* g = A + dst;
 #pragma unroll
                     for (int v = lane; v < B; v += 32) {
                         const u32 vv = jb * B + v;
-                        A[dst + v] = vv < fb ? buf[b * B + vv] : tile[ob + vv - fb];
+                        g[v] = vv < fb ? buf[b * B + vv] : tile[ob + vv - fb];
                     }
                 } else if (lane == 0) {
                     set_status(ws.ctr, kStatusInternal);
                 }
             }
             __syncthreads();
-            // the remainder of each bucket goes (back) into its buffer block
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (bk[q] >= 0) {
-                    const int b = bk[q];
-                    const u32 fb = s_fill[b], cb = s_cnt[b];
-                    const u32 nf = (fb + cb) / B;
-                    const u32 p = fb + rk[q];
-                    if (p >= nf * B) buf[b * B + (p - nf * B)] = e[q];
-                }
+            // the remainder of a bucket that emitted blocks goes back into its
+            // buffer block (one warp per such bucket)
+            for (u32 i = warp; i < n_emit; i += NW) {
+                const u32 b = s_emit[i];
+                const u32 fb = s_fill[b], cb = s_cnt[b];
+                const u32 nf = (fb + cb) / B, rem = (fb + cb) % B;
+                const u32 from = s_off[b] + nf * B - fb;
+                for (u32 v = lane; v < rem; v += 32) buf[b * B + v] = tile[from + v];
             }
             __syncthreads();
             if (tid < kMaxBuckets) {
