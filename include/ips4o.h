@@ -130,6 +130,26 @@ ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream,
                              uint64_t* h_bounds, size_t* num_buckets,
                              uint64_t* h_splitters, size_t* num_splitters, int* eq);
 
+/* Sort d_ptr[0..n) in place, like ips4o_sort, without allocating any memory.
+ * The paper has no counterpart: this entry point serves callers that cannot
+ * allocate when they sort (for example while a stream is being captured into
+ * a CUDA graph, or a service whose device memory is fixed at start-up).
+ * Instead of the workspace it uses a scratch area built into the library: a
+ * 16 MiB __device__ array, which every GPU that loads the library holds until
+ * the process exits, plus a static host staging buffer.
+ *   - n is limited to 2^20 elements; larger n returns IPS4O_ERR_TOO_LARGE
+ *     before any work is queued.  The library's default parameters are used
+ *     (ips4o_set_params does not apply), and ips4o_get_stats does not report
+ *     these calls.
+ *   - The first call on a device looks up the device address of the scratch
+ *     array (cudaGetSymbolAddress); make that first call before any stream
+ *     capture.
+ *   - All calls share the scratch array and keep the last call's contents;
+ *     calls are serialised by the library and each waits for its own work, so
+ *     calls must not overlap on the GPU (they would race on the scratch).
+ *   - Same argument checks and return codes as ips4o_sort. */
+ips4o_status ips4o_sort_noalloc(void* d_ptr, size_t n, int key_type, void* stream);
+
 /* Device workspace the library needs for a sort of n elements of the type. */
 size_t ips4o_workspace_bytes(size_t n, int key_type);
 

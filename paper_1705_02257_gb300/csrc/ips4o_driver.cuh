@@ -166,6 +166,7 @@ struct Driver {
     std::vector<Timed> timed;
 
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
+    Driver(DeviceState& s, cudaStream_t strm, const ips4o_params& p) : st(s), stream(strm), prm(p) {}
 
     ips4o_status setup(u64 n) {
         caps = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));

@@ -71,6 +71,8 @@ def _load():
     lib.ips4o_sort.argtypes = [vp, sz, i32, vp]
     lib.ips4o_sort_host.restype = i32
     lib.ips4o_sort_host.argtypes = [vp, sz, i32, vp]
+    lib.ips4o_sort_noalloc.restype = i32
+    lib.ips4o_sort_noalloc.argtypes = [vp, sz, i32, vp]
     lib.ips4o_partition.restype = i32
     lib.ips4o_partition.argtypes = [vp, sz, i32, vp, vp, ctypes.POINTER(sz), vp, ctypes.POINTER(sz),
                                     ctypes.POINTER(i32)]
@@ -107,6 +109,11 @@ def ips4o_sort(d_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
 
 def ips4o_sort_host(h_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
     return _lib.ips4o_sort_host(h_ptr, n, key_type, stream)
+
+
+def ips4o_sort_noalloc(d_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
+    """The sort without any memory allocation (fixed scratch, n <= 2^20)."""
+    return _lib.ips4o_sort_noalloc(d_ptr, n, key_type, stream)
 
 
 def ips4o_partition(d_ptr: int, n: int, key_type: int, stream: int = 0):
