@@ -179,6 +179,10 @@ def run_gpu(args):
     work = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
     ips4o.reset_params()
+    base_params = {}
+    if args.stripes_per_sm > 0:
+        base_params["stripes_per_sm"] = args.stripes_per_sm
+        ips4o.set_params(**base_params)
 
     def one_step():
         work.copy_(pristine)
@@ -217,7 +221,7 @@ def run_gpu(args):
     sorted_ok = bool(np.all(out[1:] >= out[:-1]))
 
     # per-kernel times (CUDA events around each launch on the sort's stream)
-    ips4o.set_params(profile=1)
+    ips4o.set_params(profile=1, **base_params)
     prof_steps = max(1, min(3, args.steps))
     phase_ms = {p: 0.0 for p in ips4o.PHASES}
     phase_launches = {p: 0 for p in ips4o.PHASES}
@@ -228,6 +232,8 @@ def run_gpu(args):
             phase_ms[p] += st["phase_ms"][p]
             phase_launches[p] += st["phase_launches"][p]
     ips4o.reset_params()
+    if base_params:
+        ips4o.set_params(**base_params)
     elem = 8
     # algorithmic bytes per launch (Appendix B I/O volume): classification and
     # block permutation each read and write the elements of the launch once.
@@ -317,6 +323,7 @@ def main():
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--stripes-per-sm", type=int, default=0, help="override the library's stripes per SM")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

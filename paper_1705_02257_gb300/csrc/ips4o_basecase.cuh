@@ -99,9 +99,8 @@ struct BaseCfg {
     static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
     static constexpr int LIMIT = 64;         // any larger sub-bucket: whole-bucket bitonic fallback
     static constexpr size_t off_data = 0;
-    static constexpr size_t off_cnt = off_data + (size_t)CAP * sizeof(E);
-    static constexpr size_t off_off = off_cnt + MAXSUB * 4;
-    static constexpr size_t off_tmp = off_off + MAXSUB * 4;
+    static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[MAXSUB + 1]
+    static constexpr size_t off_tmp = off_off + (MAXSUB + 1) * 4 + 12;
     static constexpr size_t smem_bytes = off_tmp + 64 * 8;
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
@@ -112,7 +111,7 @@ struct BaseCfg {
 
 // The two size classes: most buckets (at most kBaseSmall elements) are
 // sorted by 512-thread CTAs that fit two per SM; the rare larger ones (up to
-// kBaseCap) by 1024-thread CTAs with 128 KiB of shared memory.
+// kBaseCap) by 1024-thread CTAs.
 template <class T>
 using BaseSmall = BaseCfg<T, 512, T::kBaseSmall>;
 template <class T>
@@ -169,8 +168,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     constexpr int TPB = C::TPB, EPT = C::EPT, SPT = C::SUBS_PER_THREAD;
     if (m < 2) return;
     E* data = (E*)(smem + C::off_data);
-    u32* cnt = (u32*)(smem + C::off_cnt);
-    u32* off = (u32*)(smem + C::off_off);
+    u32* off = (u32*)(smem + C::off_off);          // sub-bucket sizes, then (scanned) starts
     u64* tmp = (u64*)(smem + C::off_tmp);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
@@ -187,7 +185,8 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         }
     }
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) cnt[tid * SPT + q] = 0;
+    for (int q = 0; q < SPT; ++q) off[tid * SPT + q] = 0;
+    if (tid == 0) off[C::MAXSUB] = 0;
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -227,16 +226,17 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
         if (idx < m) {
-            const u32 r = atomicAdd(&cnt[sub_of(T::key(e[q]))], 1u);
+            const u32 r = atomicAdd(&off[sub_of(T::key(e[q]))], 1u);
             rk2[q / 2] |= r << (16 * (q & 1));
         }
     }
     __syncthreads();
-    // exclusive scan of the sub-bucket sizes (SPT consecutive entries per thread)
+    // exclusive scan of the sub-bucket sizes in place (SPT consecutive entries
+    // per thread); off[MAXSUB] receives the total
     u32 c[SPT], csum = 0, cmax = 0;
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
-        c[q] = cnt[tid * SPT + q];
+        c[q] = off[tid * SPT + q];
         csum += c[q];
         cmax = c[q] > cmax ? c[q] : cmax;
     }
@@ -248,6 +248,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         off[tid * SPT + q] = pre;
         pre += c[q];
     }
+    if (tid == TPB - 1) off[C::MAXSUB] = pre;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
@@ -275,9 +276,9 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
                 const E x = data[i];
                 const K k = T::key(x);
                 const u32 sb = sub_of(k);
-                const u32 o = off[sb], n_sb = cnt[sb];
+                const u32 o = off[sb], o1 = off[sb + 1];
                 u32 r = 0;
-                for (u32 jj = o; jj < o + n_sb; ++jj) {
+                for (u32 jj = o; jj < o1; ++jj) {
                     const K kj = T::key(data[jj]);
                     r += (kj < k || (kj == k && jj < i)) ? 1u : 0u;
                 }

@@ -124,18 +124,51 @@ __device__ __forceinline__ void classify_fixed(const K (&k)[IPT], const K* tree,
     }
 }
 
-template <class K, int IPT>
-__device__ __forceinline__ void classify_many(const K (&k)[IPT], const K* tree, const K* spl, int logL, bool eq,
-                                              int (&bk)[IPT]) {
+// The same descent over a tree of 64-bit keys kept as two 32-bit halves:
+// a_j <= e is decided on the high halves, and the low half of a_j is read
+// only when the high halves are equal, so most steps move 4 bytes per lane
+// through shared memory instead of 8.
+template <int IPT, int LOGL>
+__device__ __forceinline__ void classify_fixed_split(const u64 (&k)[IPT], const u32* thi, const u32* tlo,
+                                                     const u64* spl, bool eq, int (&bk)[IPT]) {
+    int j[IPT];
+    u32 khi[IPT], klo[IPT];
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        j[q] = 1;
+        khi[q] = (u32)(k[q] >> 32);
+        klo[q] = (u32)k[q];
+    }
+#pragma unroll
+    for (int l = 0; l < LOGL; ++l) {
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const u32 ah = thi[j[q]];
+            bool le = ah < khi[q];
+            if (ah == khi[q]) le = tlo[j[q]] <= klo[q];
+            j[q] = 2 * j[q] + (le ? 1 : 0);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < IPT; ++q) {
+        int i = j[q] - (1 << LOGL);
+        if (eq) i = 2 * i - ((i > 0 && spl[i] == k[q]) ? 1 : 0);
+        bk[q] = i;
+    }
+}
+
+template <int IPT>
+__device__ __forceinline__ void classify_many(const u64 (&k)[IPT], const u32* thi, const u32* tlo, const u64* spl,
+                                              int logL, bool eq, int (&bk)[IPT]) {
     switch (logL) {
-    case 8: classify_fixed<K, IPT, 8>(k, tree, spl, eq, bk); break;
-    case 7: classify_fixed<K, IPT, 7>(k, tree, spl, eq, bk); break;
-    case 6: classify_fixed<K, IPT, 6>(k, tree, spl, eq, bk); break;
-    case 5: classify_fixed<K, IPT, 5>(k, tree, spl, eq, bk); break;
-    case 4: classify_fixed<K, IPT, 4>(k, tree, spl, eq, bk); break;
-    case 3: classify_fixed<K, IPT, 3>(k, tree, spl, eq, bk); break;
-    case 2: classify_fixed<K, IPT, 2>(k, tree, spl, eq, bk); break;
-    default: classify_fixed<K, IPT, 1>(k, tree, spl, eq, bk); break;
+    case 8: classify_fixed_split<IPT, 8>(k, thi, tlo, spl, eq, bk); break;
+    case 7: classify_fixed_split<IPT, 7>(k, thi, tlo, spl, eq, bk); break;
+    case 6: classify_fixed_split<IPT, 6>(k, thi, tlo, spl, eq, bk); break;
+    case 5: classify_fixed_split<IPT, 5>(k, thi, tlo, spl, eq, bk); break;
+    case 4: classify_fixed_split<IPT, 4>(k, thi, tlo, spl, eq, bk); break;
+    case 3: classify_fixed_split<IPT, 3>(k, thi, tlo, spl, eq, bk); break;
+    case 2: classify_fixed_split<IPT, 2>(k, thi, tlo, spl, eq, bk); break;
+    default: classify_fixed_split<IPT, 1>(k, thi, tlo, spl, eq, bk); break;
     }
 }
 
@@ -170,8 +203,12 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
         const SubDesc sub = ws.subs[sd.sub];
         const int logL = (int)sub.log_leaves;
         const bool eq = sub.eq != 0;
+        u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
+        u32* s_tlo = s_thi + kMaxLeaves;
         for (int i = tid; i < kMaxLeaves; i += TPB) {
-            s_tree[i] = ws.tree[(u64)sd.sub * kMaxLeaves + i];
+            const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
+            s_thi[i] = (u32)(a >> 32);
+            s_tlo[i] = (u32)a;
             s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
         }
         for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
@@ -213,7 +250,7 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
                 e[q] = tile[idx < tcount ? idx : 0];
                 k[q] = T::key(e[q]);
             }
-            classify_many<K, IPT>(k, s_tree, s_spl, logL, eq, bk);
+            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (tid + q * TPB >= tcount) bk[q] = -1;
