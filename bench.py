@@ -7,6 +7,9 @@ than the 129 MB L2, so no flush is needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--dist uniform]
   python bench.py --impl reference     # the CPU oracle on a bounded sample
+  python bench.py --workload batched [--segments 100000 | --batched-total-log2 28] [--dist two_dup]
+      many independent arrays (log-uniform lengths in [16, 2^20]) sorted by
+      one ips4o_sort_segmented call per step, against a loop of plain calls
 
 Prints one JSON line.  `value` is keys/s over all ranks (N > 1 runs
 independent replicas, one per GPU: the sort does not shard).
@@ -311,6 +314,182 @@ def run_gpu(args):
     return 0
 
 
+def _segment_lengths(args, inputs):
+    """Log-uniform lengths floor(2^U), U ~ U[4, 20] (seed 4): either a fixed
+    number of arrays or as many as it takes to reach 2^batched_total_log2 keys."""
+    if args.batched_total_log2 <= 0:
+        return inputs.log_uniform_lengths(args.segments, 4, 20)
+    target = 1 << args.batched_total_log2
+    count = 4096
+    while True:
+        lengths = inputs.log_uniform_lengths(count, 4, 20)
+        csum = np.cumsum(lengths)
+        if csum[-1] >= target:
+            return lengths[: int(np.searchsorted(csum, target)) + 1]
+        count *= 2
+
+
+def run_batched(args):
+    import torch
+    rank, world, local = _dist_env()
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1705_02257_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1705_02257_gb300 import inputs, ips4o
+    import oracle
+
+    lengths = _segment_lengths(args, inputs)
+    nseg = len(lengths)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.uint64)
+    total = int(off[-1])
+    pristine = torch.empty(total, dtype=torch.int64, device="cuda")
+    work = torch.empty_like(pristine)
+    # generate on the host in groups of at most 2^27 keys, copy into HBM
+    group = 1 << 27
+    h_buf = torch.empty(group + (1 << 20), dtype=torch.int64).pin_memory()
+    h_np = h_buf.numpy().view(np.uint64)
+    j = 0
+    while j < nseg:
+        j1 = j
+        while j1 < nseg and (j1 == j or off[j1 + 1] - off[j] <= group):
+            j1 += 1
+        cnt = int(off[j1] - off[j])
+        buf = h_np if cnt <= h_np.size else np.empty(cnt, dtype=np.uint64)
+        inputs.u64_segments(lengths[j:j1], args.dist, first=j, out=buf)
+        src = torch.from_numpy(buf[:cnt].view(np.int64))
+        pristine[int(off[j]):int(off[j1])].copy_(src)
+        torch.cuda.synchronize()
+        j = j1
+    stream = torch.cuda.current_stream()
+    ips4o.reset_params()
+    off_host = np.ascontiguousarray(off)
+
+    def one_step():
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        rc = ips4o.ips4o_sort_segmented(work.data_ptr(), off_host.ctypes.data, nseg, ips4o.U64, stream.cuda_stream)
+        e.record(stream)
+        torch.cuda.synchronize()
+        if rc:
+            raise ips4o.Ips4oError(rc, "ips4o_sort_segmented")
+        return s.elapsed_time(e)
+
+    for _ in range(args.warmup):
+        one_step()
+    if dist_on:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        times = [one_step() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    total_ms = sum(times)
+    if dist_on:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    stats = ips4o.stats()
+    value = total * world * args.steps / (total_ms * 1e-3)
+
+    # parity on the last timed step: every segment non-decreasing (on the
+    # device), and a seeded sample of segments equal to the oracle's sort
+    sorted_ok = True
+    seg_starts = off[1:-1].astype(np.int64)
+    chunk = 1 << 28
+    for c0 in range(0, total - 1, chunk):
+        c1 = min(total, c0 + chunk + 1)
+        x = work[c0:c1] ^ (-(1 << 63))          # unsigned order as signed order
+        desc = x[1:] < x[:-1]                   # desc[i]: element c0+i+1 below its predecessor
+        lo, hi = np.searchsorted(seg_starts, [c0 + 1, c1])
+        if hi > lo:
+            desc[torch.from_numpy(seg_starts[lo:hi] - c0 - 1).cuda()] = False   # a new array starts there
+        if bool(desc.any().item()):
+            sorted_ok = False
+        del x, desc
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(nseg, size=min(nseg, args.verify_segments), replace=False))
+    oracle_ok = True
+    for q in sample:
+        lo, hi = int(off[q]), int(off[q + 1])
+        got = work[lo:hi].cpu().numpy().view(np.uint64)
+        src = pristine[lo:hi].cpu().numpy().view(np.uint64)
+        if not np.array_equal(got, oracle.sort(src, "u64")):
+            oracle_ok = False
+            break
+
+    # the same arrays through a loop of plain ips4o_sort calls
+    lib = ips4o.lib()
+    base = work.data_ptr()
+    sptr = stream.cuda_stream
+
+    def plain_loop(count):
+        work.copy_(pristine)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q in range(count):
+            rc = lib.ips4o_sort(base + 8 * int(off[q]), int(lengths[q]), ips4o.U64, sptr)
+            if rc:
+                raise ips4o.Ips4oError(rc, "ips4o_sort")
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    plain_loop(min(nseg, 2000))
+    plain_s = plain_loop(nseg)
+    plain_value = total / plain_s
+
+    if rank != 0:
+        if dist_on:
+            tdist.destroy_process_group()
+        return 0
+    # the oracle on the host cores: the first arrays of the batch up to ~2^24 keys
+    cpu = None
+    if not args.no_cpu_baseline:
+        k = int(np.searchsorted(off, 1 << 24)) or 1
+        keys = int(off[k])
+        data = inputs.u64_segments(lengths[:k], args.dist)
+        t0 = time.perf_counter()
+        for q in range(k):
+            oracle.sort(data[int(off[q]):int(off[q + 1])], "u64")
+        dt = time.perf_counter() - t0
+        cpu = {"value": keys / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+               "sample": f"the batch's first {k} arrays ({keys} keys), one oracle call each, single-threaded C oracle"}
+    peak, peak_kind = _peaks()
+    alg = (4 * stats["elements_distributed"] + 2 * total) * 8
+    ms = total_ms / args.steps
+    achieved = alg / (ms * 1e-3) / 1e9
+    label = (f"{nseg} uint64 arrays" if args.batched_total_log2 <= 0
+             else f"{nseg} uint64 arrays (lengths drawn until 2^{args.batched_total_log2} keys)")
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": f"batched segmented sort: {label}, log-uniform lengths [16, 2^20] (seed 4), "
+                               f"{args.dist} keys per array, one ips4o_sort_segmented call",
+                   "segments": nseg, "n": total, "key_type": "u64", "distribution": args.dist,
+                   "l2": f"{total * 8 / 2**30:.1f} GiB per step, larger than L2",
+                   "parallelism": f"replicas x{world}"},
+        "vs_plain_loop": {"value": plain_value, "unit": METRIC, "ratio": value / plain_value,
+                          "ms": plain_s * 1e3, "calls": nseg},
+        "roofline": {"bound": "hbm", "kernel": "whole call", "achieved": achieved, "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / peak, "traffic": None,
+                     "alg_bytes": alg, "elements_distributed": stats["elements_distributed"]},
+        "cpu_baseline": cpu, "e2e": None, "clocks": clk.summary(),
+        "gpu_launches": stats["kernel_launches"] * args.steps,
+        "output_sorted": sorted_ok, "oracle_sample_ok": oracle_ok, "oracle_sample_segments": int(len(sample)),
+        "stats": {k: stats[k] for k in ("levels", "chunks", "subproblems", "blocks_moved", "base_case_buckets",
+                                        "workspace_bytes")},
+    }
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        tdist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -324,9 +503,16 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes-per-sm", type=int, default=0, help="override the library's stripes per SM")
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--segments", type=int, default=100_000, help="batched: number of arrays")
+    ap.add_argument("--batched-total-log2", type=int, default=0,
+                    help="batched: draw arrays until this many keys (2^x) instead of --segments")
+    ap.add_argument("--verify-segments", type=int, default=200, help="batched: arrays checked against the oracle")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
     return run_gpu(args)
 
 

@@ -19,14 +19,17 @@
  *     frees or keeps them after the call returns.
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *     stream).  Work is enqueued on it.
- *   - The library owns a per-device workspace (see ips4o_workspace_bytes),
- *     allocated on first use with cudaMalloc and reused; its size is
- *     O(k*b*t + number of subproblems) as in Theorem 2, plus a small host
- *     staging area.
- *   - Calls on the same device are serialised by the library (one workspace
- *     per device).  They are not capturable in a CUDA graph: the host driver
- *     reads the number of subproblems of each recursion level back from the
- *     device before it launches the next level.
+ *   - The library owns one workspace per (device, stream) pair (see
+ *     ips4o_workspace_bytes), allocated on first use with cudaMalloc and
+ *     reused; its size is O(k*b*t + number of subproblems) as in Theorem 2,
+ *     plus a small host staging area.
+ *   - Calls on the same (device, stream) are serialised by the library;
+ *     calls on different streams, made from different host threads, run
+ *     side by side on the device, each with its own workspace.  Calls are not
+ *     capturable in a CUDA graph: the host driver reads the number of
+ *     subproblems of each recursion level back from the device before it
+ *     launches the next level (ips4o_sort_noalloc is the exception for the
+ *     allocation part only).
  *   - Return codes: argument errors are detected before any work is queued;
  *     device-side errors (an exhausted bounded wait, a broken internal
  *     invariant) are reported by the call that detects them through the
@@ -130,6 +133,37 @@ ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream,
                              uint64_t* h_bounds, size_t* num_buckets,
                              uint64_t* h_splitters, size_t* num_splitters, int* eq);
 
+/* Sort many independent segments of one device array, each in place and
+ * each as ips4o_sort would sort it alone (the paper has no batched form; its
+ * recursion already processes the buckets of a level side by side, Section
+ * 4, and this entry point starts that processing from the caller's
+ * segments).  Segment i is d_base[offsets[i] .. offsets[i+1]), i <
+ * num_segments; offsets holds num_segments + 1 non-decreasing element
+ * indices, in host or device memory (it is read once at the start of the
+ * call).  Elements outside the segments are not touched.  Segments no
+ * larger than the base case (ips4o_base_case_capacity) are sorted in shared
+ * memory by one launch; the others go through the distribution levels
+ * together, one set of kernel launches per level for all of them.
+ * Errors: decreasing offsets or a null d_base with elements -> INVALID_ARG;
+ * a segment above the ips4o_sort size limit -> TOO_LARGE (nothing queued).
+ * Synchronises the stream; on return the segments are sorted. */
+ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t num_segments, int key_type,
+                                  void* stream);
+
+/* Sort `count` separate device arrays, ptrs[i][0 .. lens[i]), each in place,
+ * in one call (the same processing as ips4o_sort_segmented).  ptrs and lens
+ * are arrays of `count` entries in host or device memory; every ptrs[i] with
+ * lens[i] > 0 must be aligned for the key type, and the arrays must not
+ * overlap (INVALID_ARG otherwise, before any work).  Arrays of length 0 are
+ * skipped. */
+ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t count, int key_type,
+                                void* stream);
+
+/* Waits for all work on `stream` and reports a CUDA error that it raised
+ * (IPS4O_ERR_CUDA, text in ips4o_last_cuda_error), else IPS4O_OK.  The sort
+ * calls already return device-side errors themselves. */
+ips4o_status ips4o_stream_status(void* stream);
+
 /* Sort d_ptr[0..n) in place, like ips4o_sort, without allocating any memory.
  * The paper has no counterpart: this entry point serves callers that cannot
  * allocate when they sort (for example while a stream is being captured into
@@ -153,14 +187,14 @@ ips4o_status ips4o_sort_noalloc(void* d_ptr, size_t n, int key_type, void* strea
 /* Device workspace the library needs for a sort of n elements of the type. */
 size_t ips4o_workspace_bytes(size_t n, int key_type);
 
-/* Free the workspace and staging buffers held on the current device. */
+/* Free the workspaces and staging buffers held on the current device (all streams). */
 ips4o_status ips4o_release_workspace(void);
 
 /* Parameters (process-wide).  ips4o_set_params(NULL) restores defaults. */
 ips4o_status ips4o_set_params(const ips4o_params* p);
 ips4o_status ips4o_get_params(ips4o_params* out);
 
-/* Counters of the last call made by this process on the current device. */
+/* Counters of the last call made by this process on the current device (any stream). */
 ips4o_status ips4o_get_stats(ips4o_stats* out);
 
 /* Capacity of the shared-memory base case for a key type, in elements. */

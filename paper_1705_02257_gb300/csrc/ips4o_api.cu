@@ -4,9 +4,13 @@
 // and dispatch on the element type to the per-type drivers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "ips4o_common.cuh"
 #include "ips4o_host.h"
@@ -15,7 +19,10 @@ namespace ips4o {
 
 namespace {
 std::mutex g_mtx;
-DeviceState* g_states[64] = {nullptr};
+// one state (workspace, staging, stats) per (device, stream): calls on
+// different streams run side by side, calls on one stream are serialised
+std::map<std::pair<int, uintptr_t>, DeviceState*> g_states;
+ips4o_stats g_last_stats[64];
 ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
 thread_local char g_last_err[256] = {0};
 }  // namespace
@@ -28,20 +35,28 @@ void set_last_cuda_error(cudaError_t e, const char* where) {
     std::snprintf(g_last_err, sizeof g_last_err, "%s: %s (%d)", where, cudaGetErrorString(e), (int)e);
 }
 
-DeviceState* current_device_state(cudaError_t* err) {
+DeviceState* stream_state(void* stream, cudaError_t* err) {
     int dev = 0;
     *err = cudaGetDevice(&dev);
     if (*err != cudaSuccess) return nullptr;
     if (dev < 0 || dev >= 64) { *err = cudaErrorInvalidDevice; return nullptr; }
     std::lock_guard<std::mutex> lk(g_mtx);
-    if (!g_states[dev]) {
+    DeviceState*& slot = g_states[std::make_pair(dev, (uintptr_t)stream)];
+    if (!slot) {
         DeviceState* s = new DeviceState();
         s->device = dev;
         *err = cudaDeviceGetAttribute(&s->sms, cudaDevAttrMultiProcessorCount, dev);
         if (*err != cudaSuccess) { delete s; return nullptr; }
-        g_states[dev] = s;
+        slot = s;
     }
-    return g_states[dev];
+    return slot;
+}
+
+DeviceState* current_device_state(cudaError_t* err) { return stream_state(nullptr, err); }
+
+static void publish_stats(const DeviceState& st) {
+    std::lock_guard<std::mutex> lk(g_mtx);
+    g_last_stats[st.device] = st.stats;
 }
 
 ips4o_status ensure_device_buffer(void** ptr, size_t* have, size_t need) {
@@ -102,12 +117,52 @@ static ips4o_status check_args(const void* p, size_t n, int kt) {
 }
 
 static ips4o_status dispatch(DeviceState& st, void* d, size_t n, int kt, cudaStream_t s, PartitionOut* part) {
+    ips4o_status rc;
     switch (kt) {
-    case IPS4O_U64: return sort_u64(st, d, n, s, part);
-    case IPS4O_F64: return sort_f64(st, d, n, s, part);
-    case IPS4O_PAIR_U64: return sort_pair(st, d, n, s, part);
+    case IPS4O_U64: rc = sort_u64(st, d, n, s, part); break;
+    case IPS4O_F64: rc = sort_f64(st, d, n, s, part); break;
+    case IPS4O_PAIR_U64: rc = sort_pair(st, d, n, s, part); break;
     default: return IPS4O_ERR_UNSUPPORTED_TYPE;
     }
+    publish_stats(st);
+    return rc;
+}
+
+static ips4o_status dispatch_segments(DeviceState& st, void* d, const std::vector<Task>& segs, int kt,
+                                      cudaStream_t s) {
+    ips4o_status rc;
+    switch (kt) {
+    case IPS4O_U64: rc = sort_segments_u64(st, d, segs, s); break;
+    case IPS4O_F64: rc = sort_segments_f64(st, d, segs, s); break;
+    case IPS4O_PAIR_U64: rc = sort_segments_pair(st, d, segs, s); break;
+    default: return IPS4O_ERR_UNSUPPORTED_TYPE;
+    }
+    publish_stats(st);
+    return rc;
+}
+
+// Reads `count` 8-byte values from host or device memory (unified addressing).
+static ips4o_status read_u64s(const void* src, size_t count, std::vector<uint64_t>* out, cudaStream_t s) {
+    out->resize(count);
+    if (count == 0) return IPS4O_OK;
+    cudaPointerAttributes attr;
+    cudaError_t e = cudaPointerGetAttributes(&attr, src);
+    cudaGetLastError();   // a plain host pointer may leave a query error behind
+    const bool on_device = e == cudaSuccess && (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    if (!on_device) {
+        std::memcpy(out->data(), src, count * 8);
+        return IPS4O_OK;
+    }
+    e = cudaMemcpyAsync(out->data(), src, count * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(segment table)"); return IPS4O_ERR_CUDA; }
+    return IPS4O_OK;
+}
+
+// Per-segment limits: the same as one ips4o_sort call.
+static ips4o_status check_segment(size_t n, int kt) {
+    if (n > ((size_t)16 << 30) / elem_size(kt)) return IPS4O_ERR_TOO_LARGE;
+    return IPS4O_OK;
 }
 
 }  // namespace ips4o
@@ -127,12 +182,70 @@ ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream) {
     return dispatch(*st, d_ptr, n, key_type, (cudaStream_t)stream, nullptr);
 }
 
+ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t num_segments, int key_type,
+                                  void* stream) {
+    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (num_segments == 0) return IPS4O_OK;
+    if (!offsets) return IPS4O_ERR_INVALID_ARG;
+    if (d_base && ((uintptr_t)d_base % elem_size(key_type)) != 0) return IPS4O_ERR_MISALIGNED;
+    cudaError_t e;
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    std::vector<uint64_t> off;
+    ips4o_status rc = read_u64s(offsets, num_segments + 1, &off, (cudaStream_t)stream);
+    if (rc != IPS4O_OK) return rc;
+    std::vector<Task> segs(num_segments);
+    for (size_t i = 0; i < num_segments; ++i) {
+        if (off[i + 1] < off[i]) return IPS4O_ERR_INVALID_ARG;
+        rc = check_segment(off[i + 1] - off[i], key_type);
+        if (rc != IPS4O_OK) return rc;
+        segs[i] = Task{off[i], off[i + 1] - off[i]};
+    }
+    if (off[num_segments] > off[0] && !d_base) return IPS4O_ERR_INVALID_ARG;
+    return dispatch_segments(*st, d_base, segs, key_type, (cudaStream_t)stream);
+}
+
+ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t count, int key_type, void* stream) {
+    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (count == 0) return IPS4O_OK;
+    if (!ptrs || !lens) return IPS4O_ERR_INVALID_ARG;
+    const size_t es = elem_size(key_type);
+    cudaError_t e;
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    std::vector<uint64_t> p, n;
+    ips4o_status rc = read_u64s(ptrs, count, &p, (cudaStream_t)stream);
+    if (rc == IPS4O_OK) rc = read_u64s(lens, count, &n, (cudaStream_t)stream);
+    if (rc != IPS4O_OK) return rc;
+    // the arrays as segments of one address range starting at the lowest of them
+    std::vector<std::pair<uint64_t, uint64_t>> arr;
+    arr.reserve(count);
+    for (size_t i = 0; i < count; ++i) {
+        if (n[i] == 0) continue;
+        if (!p[i]) return IPS4O_ERR_INVALID_ARG;
+        if (p[i] % es) return IPS4O_ERR_MISALIGNED;
+        rc = check_segment(n[i], key_type);
+        if (rc != IPS4O_OK) return rc;
+        arr.emplace_back(p[i], n[i]);
+    }
+    if (arr.empty()) return IPS4O_OK;
+    std::sort(arr.begin(), arr.end());
+    for (size_t i = 0; i + 1 < arr.size(); ++i)
+        if (arr[i].first + arr[i].second * es > arr[i + 1].first) return IPS4O_ERR_INVALID_ARG;   // overlap
+    const uint64_t base = arr[0].first;
+    std::vector<Task> segs(arr.size());
+    for (size_t i = 0; i < arr.size(); ++i) segs[i] = Task{(arr[i].first - base) / es, arr[i].second};
+    return dispatch_segments(*st, (void*)(uintptr_t)base, segs, key_type, (cudaStream_t)stream);
+}
+
 ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) {
     ips4o_status rc = check_args(h_ptr, n, key_type);
     if (rc != IPS4O_OK) return rc;
     if (n < 2) return IPS4O_OK;
     cudaError_t e;
-    DeviceState* st = current_device_state(&e);
+    DeviceState* st = stream_state(stream, &e);
     if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     std::lock_guard<std::mutex> lk(st->mtx);
     const size_t bytes = n * elem_size(key_type);
@@ -156,7 +269,7 @@ ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream, 
     if (rc != IPS4O_OK) return rc;
     if (n < 2 || !h_bounds || !num_buckets || !h_splitters || !num_splitters || !eq) return IPS4O_ERR_INVALID_ARG;
     cudaError_t e;
-    DeviceState* st = current_device_state(&e);
+    DeviceState* st = stream_state(stream, &e);
     if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     std::lock_guard<std::mutex> lk(st->mtx);
     PartitionOut out{h_bounds, num_buckets, h_splitters, num_splitters, eq};
@@ -178,17 +291,25 @@ size_t ips4o_workspace_bytes(size_t n, int key_type) {
 }
 
 ips4o_status ips4o_release_workspace(void) {
-    cudaError_t e;
-    DeviceState* st = current_device_state(&e);
-    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
-    std::lock_guard<std::mutex> lk(st->mtx);
-    if (st->d_ws) cudaFree(st->d_ws);
-    if (st->d_host_copy) cudaFree(st->d_host_copy);
-    if (st->h_stage) cudaFreeHost(st->h_stage);
-    for (cudaEvent_t ev : st->events) cudaEventDestroy(ev);
-    st->events.clear();
-    st->d_ws = st->d_host_copy = st->h_stage = nullptr;
-    st->ws_bytes = st->d_host_copy_bytes = st->h_stage_bytes = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::vector<DeviceState*> mine;
+    {
+        std::lock_guard<std::mutex> lk(g_mtx);
+        for (auto& kv : g_states)
+            if (kv.first.first == dev) mine.push_back(kv.second);
+    }
+    for (DeviceState* st : mine) {
+        std::lock_guard<std::mutex> lk(st->mtx);
+        if (st->d_ws) cudaFree(st->d_ws);
+        if (st->d_host_copy) cudaFree(st->d_host_copy);
+        if (st->h_stage) cudaFreeHost(st->h_stage);
+        for (cudaEvent_t ev : st->events) cudaEventDestroy(ev);
+        st->events.clear();
+        st->d_ws = st->d_host_copy = st->h_stage = nullptr;
+        st->ws_bytes = st->d_host_copy_bytes = st->h_stage_bytes = 0;
+    }
     return IPS4O_OK;
 }
 
@@ -214,11 +335,12 @@ ips4o_status ips4o_get_params(ips4o_params* out) {
 
 ips4o_status ips4o_get_stats(ips4o_stats* out) {
     if (!out) return IPS4O_ERR_INVALID_ARG;
-    cudaError_t e;
-    DeviceState* st = current_device_state(&e);
-    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
-    std::lock_guard<std::mutex> lk(st->mtx);
-    *out = st->stats;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    if (dev < 0 || dev >= 64) return IPS4O_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mtx);
+    *out = g_last_stats[dev];
     return IPS4O_OK;
 }
 
@@ -247,5 +369,12 @@ const char* ips4o_status_string(int s) {
 }
 
 const char* ips4o_last_cuda_error(void) { return g_last_err; }
+
+ips4o_status ips4o_stream_status(void* stream) {
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) { set_last_cuda_error(e, "ips4o_stream_status"); return IPS4O_ERR_CUDA; }
+    return IPS4O_OK;
+}
 
 }  // extern "C"

@@ -164,9 +164,11 @@ struct Workspace {
     Task* next_tasks;         // [next_cap]
     Task* base_small;         // [max_sub * 256] buckets for the small base case
     Task* base_large;         // [max_sub * 256] buckets for the large base case
+    Task* init_tasks;         // [init_cap]      segments sorted by the base case alone
+    u32* init_count;          // [2]             small / large entries of init_tasks
     ChunkCounters* ctr;       // [1]
     u32 max_sub, max_stripes;
-    u64 pool_cap, next_cap;
+    u64 pool_cap, next_cap, init_cap;
 };
 
 // ------------------------------------------------------------ primitives

@@ -33,6 +33,7 @@ template <class T>
 struct Caps {
     u32 max_sub, max_stripes;
     u64 pool_cap, next_cap;
+    u64 init_cap;       // segments that go straight to the base case (segmented calls)
 };
 
 // Base-case threshold in effect: buckets larger than this recurse.
@@ -53,8 +54,11 @@ Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
     target = std::min<u64>(target, n / kMinStripe + 1);   // stripes are at least kMinStripe long
     u64 pool = std::max<u64>(n / 32, target * kMaxBuckets * (B - 1));
     pool = std::min<u64>(pool, n + kMaxBuckets * B);
+    // a chunk never holds more leftovers than its stripes' buffers
+    pool = std::min<u64>(pool, (u64)c.max_stripes * kMaxBuckets * (B - 1));
     c.pool_cap = std::max<u64>(pool, (u64)kMaxBuckets * B);
     c.next_cap = n / (cap + 1) + 16;
+    c.init_cap = 0;
     return c;
 }
 
@@ -94,11 +98,14 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.next_tasks = (Task*)take(c.next_cap * sizeof(Task));
     w.base_small = (Task*)take(S * kMaxBuckets * sizeof(Task));
     w.base_large = (Task*)take(S * kMaxBuckets * sizeof(Task));
+    w.init_tasks = (Task*)take(c.init_cap * sizeof(Task));
+    w.init_count = (u32*)take(2 * sizeof(u32));
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.max_sub = c.max_sub;
     w.max_stripes = c.max_stripes;
     w.pool_cap = c.pool_cap;
     w.next_cap = c.next_cap;
+    w.init_cap = c.init_cap;
     if (ws) *ws = w;
     return align_up(off, 256);
 }
@@ -168,8 +175,10 @@ struct Driver {
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
     Driver(DeviceState& s, cudaStream_t strm, const ips4o_params& p) : st(s), stream(strm), prm(p) {}
 
-    ips4o_status setup(u64 n) {
+    ips4o_status setup(u64 n, u64 init_cap = 0) {
+        cudaGetLastError();   // an error left by an earlier, unrelated runtime call is not this call's
         caps = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
+        caps.init_cap = init_cap;
         const size_t need = carve<T>(caps, nullptr, nullptr);
         ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
         if (rc != IPS4O_OK) return rc;
@@ -246,8 +255,21 @@ struct Driver {
         int slot_;                                                \
         ips4o_status rc_ = ev_begin(phase, &slot_);               \
         if (rc_ != IPS4O_OK) return rc_;                          \
+        cudaError_t le_ = cudaGetLastError();                     \
+        if (le_ != cudaSuccess) {                                 \
+            char w_[64];                                          \
+            std::snprintf(w_, sizeof w_, "before launch of phase %d (driver line %d)", phase, __LINE__); \
+            set_last_cuda_error(le_, w_);                         \
+            return IPS4O_ERR_CUDA;                                \
+        }                                                         \
         __VA_ARGS__;                                              \
-        IPS4O_CUDA(cudaGetLastError());                           \
+        le_ = cudaGetLastError();                                 \
+        if (le_ != cudaSuccess) {                                 \
+            char w_[64];                                          \
+            std::snprintf(w_, sizeof w_, "launch of phase %d (driver line %d)", phase, __LINE__); \
+            set_last_cuda_error(le_, w_);                         \
+            return IPS4O_ERR_CUDA;                                \
+        }                                                         \
         rc_ = ev_end(slot_);                                      \
         if (rc_ != IPS4O_OK) return rc_;                          \
     } while (0)
@@ -292,7 +314,7 @@ struct Driver {
     }
 
     // Plan one chunk starting at tasks[i0]; returns the number of tasks taken.
-    size_t plan_chunk(const std::vector<Task>& tasks, size_t i0, u64 level_total, u32 level, bool partition,
+    size_t plan_chunk(const Task* tasks, size_t count, size_t i0, u64 level_total, u32 level, bool partition,
                       u32* nsub_out, u32* nstripes_out) {
         const u64 B = T::kBlock;
         const u64 target = (u64)std::max(1, prm.stripes_per_sm) * (u64)st.sms;
@@ -301,7 +323,7 @@ struct Driver {
         u32 nsub = 0, nstr = 0;
         u64 pool = 0;
         size_t i = i0;
-        for (; i < tasks.size(); ++i) {
+        for (; i < count; ++i) {
             const Task t = tasks[i];
             if (nsub >= caps.max_sub) break;
             u32 K = partition ? k_max : leaves_for(t.n, base_cap, k_max);
@@ -362,8 +384,14 @@ struct Driver {
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
                             d, ws, nsub, kSpinLimit)));
-        IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * kMaxBuckets, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nsub, kSpinLimit, partition ? 1u : 0u, rec_cap)));
+        // one cleanup CTA per (subproblem, bucket).  A subproblem planned
+        // with K >= 4 leaves has at most K buckets: without equality buckets
+        // at most K leaves, with them at most K/2 leaves and K - 1 buckets.
+        u32 kmax_chunk = 1;
+        for (u32 q = 0; q < nsub; ++q) kmax_chunk = std::max(kmax_chunk, h_subs[q].k_target);
+        const u32 bstride = std::min<u32>(kMaxBuckets, kmax_chunk >= 4 ? kmax_chunk : 2 * kmax_chunk);
+        IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * bstride, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                            d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u, rec_cap)));
         if (!partition) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
                                 d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
@@ -392,7 +420,65 @@ struct Driver {
         if (rc != IPS4O_OK) return rc;
         st.stats.n = n;
         if (!part && n <= (u64)rec_cap) return base_only(d, n);
-        std::vector<Task> level_tasks{Task{0, n}}, next;
+        return levels(d, std::vector<Task>{Task{0, n}}, part);
+    }
+
+    // Independent segments d[t.begin, t.begin + t.n) of one array, all sorted
+    // by one call: the segments no larger than the base case are sorted in
+    // shared memory straight away; the others enter the first distribution
+    // level together, so that every level is one set of launches for all of
+    // them (Section 4: subproblems of one level are processed side by side).
+    ips4o_status run_segments(E* d, const std::vector<Task>& segs) {
+        u64 total = 0, nbase = 0;
+        for (const Task& t : segs) {
+            total += t.n;
+            nbase += (t.n >= 2 && t.n <= (u64)recursion_cap<T>(prm)) ? 1 : 0;
+        }
+        ips4o_status rc = setup(total, nbase);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = total;
+        std::vector<Task> init(nbase), big;
+        u32 nsmall = 0, nlarge = 0;
+        for (const Task& t : segs) {
+            if (t.n < 2) continue;
+            if (t.n > (u64)rec_cap) big.push_back(t);
+            else if (t.n <= (u64)T::kBaseSmall) init[nsmall++] = t;
+            else init[nbase - 1 - nlarge++] = t;
+        }
+        if (nbase > 0) {
+            const u32 cnt[2] = {nsmall, nlarge};
+            // pageable sources: the copies have read them when the calls return
+            IPS4O_CUDA(cudaMemcpyAsync(ws.init_tasks, init.data(), nbase * sizeof(Task), cudaMemcpyHostToDevice,
+                                       stream));
+            IPS4O_CUDA(cudaMemcpyAsync(ws.init_count, cnt, sizeof cnt, cudaMemcpyHostToDevice, stream));
+            IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
+            const int gsmall = (int)std::min<u64>(nsmall, (u64)st.sms * 2);
+            const int glarge = (int)std::min<u64>(nlarge, (u64)st.sms);
+            if (gsmall > 0)
+                IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<gsmall, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes,
+                                                           stream>>>(d, ws.init_tasks, ws.init_count, ws.ctr)));
+            if (glarge > 0)
+                IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<glarge, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes,
+                                                           stream>>>(d, ws.init_tasks + nsmall, ws.init_count + 1,
+                                                                     ws.ctr)));
+            IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
+            IPS4O_CUDA(cudaStreamSynchronize(stream));
+            IPS4O_CUDA(cudaGetLastError());
+            st.stats.base_case_buckets += h_ctr->base_buckets;
+            rc = collect_events();
+            if (rc != IPS4O_OK) return rc;
+            rc = status_from(h_ctr->status);
+            if (rc != IPS4O_OK) return rc;
+        }
+        if (big.empty()) return IPS4O_OK;
+        // larger subproblems first: chunks then hold subproblems of similar size
+        std::sort(big.begin(), big.end(), [](const Task& a, const Task& b) { return a.n > b.n; });
+        return levels(d, std::move(big), nullptr);
+    }
+
+    ips4o_status levels(E* d, std::vector<Task> level_tasks, PartitionOut* part) {
+        ips4o_status rc = IPS4O_OK;
+        std::vector<Task> next;
         u32 level = 0;
         while (!level_tasks.empty()) {
             next.clear();
@@ -401,7 +487,8 @@ struct Driver {
             size_t i = 0;
             while (i < level_tasks.size()) {
                 u32 nsub = 0, nstr = 0;
-                size_t taken = plan_chunk(level_tasks, i, level_total, level, part != nullptr, &nsub, &nstr);
+                size_t taken = plan_chunk(level_tasks.data(), level_tasks.size(), i, level_total, level,
+                                          part != nullptr, &nsub, &nstr);
                 if (taken == 0) return IPS4O_ERR_INTERNAL;
                 u32 cnt = 0;
                 rc = run_chunk(d, nsub, nstr, part != nullptr, &cnt);
@@ -447,6 +534,12 @@ template <class T>
 ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
     Driver<T> drv(st, s);
     return drv.run((typename T::elem_t*)d, (u64)n, part);
+}
+
+template <class T>
+ips4o_status sort_segments_t(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s) {
+    Driver<T> drv(st, s);
+    return drv.run_segments((typename T::elem_t*)d, segs);
 }
 
 }  // namespace ips4o

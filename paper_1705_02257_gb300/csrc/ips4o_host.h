@@ -25,7 +25,8 @@ struct DeviceState {
     ips4o_stats stats{};
 };
 
-DeviceState* current_device_state(cudaError_t* err);
+DeviceState* stream_state(void* stream, cudaError_t* err);   // state of (current device, stream)
+DeviceState* current_device_state(cudaError_t* err);          // state of (current device, NULL stream)
 ips4o_params& global_params();
 void set_last_cuda_error(cudaError_t e, const char* where);
 void set_last_message(const char* msg);
@@ -44,6 +45,15 @@ struct PartitionOut {
 ips4o_status sort_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
 ips4o_status sort_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
 ips4o_status sort_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
+struct Task;
+ips4o_status sort_segments_u64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+ips4o_status sort_segments_f64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+ips4o_status sort_segments_pair(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+// ips4o_sort_noalloc's level loop; tasks = 2 * kNoAllocMaxTasks entries
+constexpr size_t kNoAllocMaxTasks = 256;   // subproblems per level (n / 16Ki << 256)
+ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
+ips4o_status sort_noalloc_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
+ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
 size_t workspace_bytes_u64(size_t n, int sms);
 size_t workspace_bytes_f64(size_t n, int sms);
 size_t workspace_bytes_pair(size_t n, int sms);

@@ -811,7 +811,8 @@ struct CleanupCfg {
 
 template <class T>
 __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
-    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit, u32 partition_only, u32 rec_cap) {
+    k_cleanup(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 bstride, u32 spin_limit, u32 partition_only,
+              u32 rec_cap) {
     typedef typename T::elem_t E;
     typedef CleanupCfg<T> C;
     constexpr int TPB = C::TPB, B = C::B;
@@ -824,10 +825,13 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
     if (threadIdx.x == 0) s_ticket = atomicAdd(&ws.ctr->ticket, 1u);
     __syncthreads();
     const u32 ticket = s_ticket;
-    const u32 j = ticket / kMaxBuckets, b = ticket % kMaxBuckets;
+    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
+    // largest bucket count, in increasing bucket order within a subproblem
+    const u32 j = ticket / bstride, b = ticket % bstride;
     if (j >= nsub) return;
     const SubDesc sub = ws.subs[j];
     const u32 nb = sub.nbuckets;
+    if (b == 0) IPS4O_GUARD(ws.ctr, nb <= bstride, nb, bstride);
     if (b >= nb) return;
     E* A = arr + sub.begin;
     const u64* bstart = ws.bstart + (u64)j * (kMaxBuckets + 1);

@@ -1,9 +1,18 @@
-// Instantiation of the distribution-step driver for one element type.
-#include "ips4o_driver.cuh"
+// Every instantiation of the kernels and drivers for one element type: the
+// plain, segmented and no-allocation sorts.  Keeping them in one translation
+// unit means the kernel attributes that a driver sets apply to the very
+// kernels it launches.
+#include "ips4o_noalloc_driver.cuh"
 
 namespace ips4o {
 ips4o_status sort_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
     return sort_t<TU64>(st, d, n, s, part);
+}
+ips4o_status sort_segments_u64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s) {
+    return sort_segments_t<TU64>(st, d, segs, s);
+}
+ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks) {
+    return noalloc_sort_t<TU64>(st, d, n, s, tasks);
 }
 size_t workspace_bytes_u64(size_t n, int sms) { return workspace_bytes_t<TU64>(n, sms); }
 }  // namespace ips4o

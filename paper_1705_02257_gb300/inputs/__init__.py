@@ -67,6 +67,8 @@ def _load():
             lib.gen_pair.argtypes = [u64p, u64, i32, u64, u64]
             lib.gen_rec100.restype = i32
             lib.gen_rec100.argtypes = [u64p, u64, i32, u64, u64]
+            lib.gen_u64_segments.restype = i32
+            lib.gen_u64_segments.argtypes = [u64p, u64p, u64, i32, u64, u64]
             lib.gen_log_uniform_lengths.restype = i32
             lib.gen_log_uniform_lengths.argtypes = [u64p, u64, ctypes.c_double, ctypes.c_double, u64]
             _lib = lib
@@ -124,6 +126,21 @@ def log_uniform_lengths(count: int, lo_log2: float, hi_log2: float,
     _check(_load().gen_log_uniform_lengths(out.ctypes.data, count, lo_log2, hi_log2, seed),
            "gen_log_uniform_lengths")
     return out
+
+
+def u64_segments(lengths: np.ndarray, dist: str = "uniform", seed: int = SEED_VALUES, first: int = 0,
+                 out: np.ndarray | None = None) -> np.ndarray:
+    """Independent arrays back to back: array j has lengths[j] keys of the
+    distribution drawn with value seed ``seed + 2^32 * (first + j)``."""
+    lengths = np.ascontiguousarray(lengths, dtype=np.uint64)
+    total = int(lengths.sum())
+    if out is None:
+        out = np.empty(total, dtype=np.uint64)
+    if out.dtype != np.uint64 or not out.flags.c_contiguous or out.size < total:
+        raise ValueError("out must be a contiguous uint64 array with room for every segment")
+    _check(_load().gen_u64_segments(out.ctypes.data, lengths.ctypes.data, len(lengths), _dist_id(dist), seed, first),
+           "gen_u64_segments")
+    return out[:total]
 
 
 def make(key_type: str, n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:

@@ -260,3 +260,22 @@ int gen_log_uniform_lengths(uint64_t* out, uint64_t count, double lo_log2, doubl
     }
     return 0;
 }
+
+/* Keys of a batch of independent arrays stored back to back: array j (the
+ * (first + j)-th of the batch, length lengths[j]) is gen_u64(lengths[j],
+ * dist, seed + 2^32 * (first + j)), so that every array has its own value
+ * stream and the distribution formulas use the array's own length. */
+int gen_u64_segments(uint64_t* out, const uint64_t* lengths, uint64_t count, int dist, uint64_t seed,
+                     uint64_t first) {
+    if (dist < 0 || dist >= DIST_COUNT) return -1;
+    uint64_t* starts = (uint64_t*)malloc((count + 1) * sizeof(uint64_t));
+    if (!starts) return -2;
+    starts[0] = 0;
+    for (uint64_t j = 0; j < count; ++j) starts[j + 1] = starts[j] + lengths[j];
+    int bad = 0;
+    #pragma omp parallel for schedule(dynamic, 16) reduction(| : bad)
+    for (int64_t j = 0; j < (int64_t)count; ++j)
+        bad |= gen_u64(out + starts[j], lengths[j], dist, seed + ((first + (uint64_t)j) << 32)) != 0;
+    free(starts);
+    return bad ? -3 : 0;
+}

@@ -73,6 +73,12 @@ def _load():
     lib.ips4o_sort_host.argtypes = [vp, sz, i32, vp]
     lib.ips4o_sort_noalloc.restype = i32
     lib.ips4o_sort_noalloc.argtypes = [vp, sz, i32, vp]
+    lib.ips4o_sort_segmented.restype = i32
+    lib.ips4o_sort_segmented.argtypes = [vp, vp, sz, i32, vp]
+    lib.ips4o_sort_batched.restype = i32
+    lib.ips4o_sort_batched.argtypes = [vp, vp, sz, i32, vp]
+    lib.ips4o_stream_status.restype = i32
+    lib.ips4o_stream_status.argtypes = [vp]
     lib.ips4o_partition.restype = i32
     lib.ips4o_partition.argtypes = [vp, sz, i32, vp, vp, ctypes.POINTER(sz), vp, ctypes.POINTER(sz),
                                     ctypes.POINTER(i32)]
@@ -114,6 +120,20 @@ def ips4o_sort_host(h_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
 def ips4o_sort_noalloc(d_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
     """The sort without any memory allocation (fixed scratch, n <= 2^20)."""
     return _lib.ips4o_sort_noalloc(d_ptr, n, key_type, stream)
+
+
+def ips4o_sort_segmented(d_base: int, offsets: int, num_segments: int, key_type: int, stream: int = 0) -> int:
+    """offsets: address of num_segments + 1 uint64 element indices (host or device)."""
+    return _lib.ips4o_sort_segmented(d_base, offsets, num_segments, key_type, stream)
+
+
+def ips4o_sort_batched(ptrs: int, lens: int, count: int, key_type: int, stream: int = 0) -> int:
+    """ptrs, lens: addresses of `count` device pointers and uint64 lengths (host or device)."""
+    return _lib.ips4o_sort_batched(ptrs, lens, count, key_type, stream)
+
+
+def ips4o_stream_status(stream: int = 0) -> int:
+    return _lib.ips4o_stream_status(stream)
 
 
 def ips4o_partition(d_ptr: int, n: int, key_type: int, stream: int = 0):
@@ -194,6 +214,49 @@ def sort(t, key_type="u64", stream: int | None = None):
     if rc:
         raise Ips4oError(rc, "ips4o_sort")
     return t
+
+
+def sort_segmented(t, offsets, key_type="u64", stream: int | None = None):
+    """Sort the segments t[offsets[i]:offsets[i+1]] of a contiguous CUDA
+    tensor (viewed as elements of ``key_type``) independently, in place.
+    ``offsets`` is a sequence or array of num_segments + 1 element indices
+    (host memory) or a uint64/int64 CUDA tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    kt = _kt(key_type)
+    if hasattr(offsets, "is_cuda") and offsets.is_cuda:
+        if offsets.element_size() != 8 or not offsets.is_contiguous():
+            raise ValueError("offsets tensor must be contiguous 64-bit")
+        addr, count, keep = offsets.data_ptr(), offsets.numel() - 1, offsets
+    else:
+        keep = np.ascontiguousarray(np.asarray(offsets, dtype=np.uint64))
+        addr, count = keep.ctypes.data, len(keep) - 1
+    if count < 0:
+        raise ValueError("offsets needs at least one entry")
+    if len(keep) and int(keep[-1]) > _count(t, kt):
+        raise ValueError("segments extend past the tensor")
+    rc = ips4o_sort_segmented(t.data_ptr(), addr, count, kt, _stream_of(t) if stream is None else stream)
+    if rc:
+        raise Ips4oError(rc, "ips4o_sort_segmented")
+    return t
+
+
+def sort_batched(tensors, key_type="u64", stream: int | None = None):
+    """Sort each contiguous CUDA tensor of ``tensors`` in place, in one call."""
+    kt = _kt(key_type)
+    tensors = list(tensors)
+    if not tensors:
+        return tensors
+    for t in tensors:
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("expected contiguous CUDA tensors")
+    ptrs = np.array([t.data_ptr() for t in tensors], dtype=np.uint64)
+    lens = np.array([_count(t, kt) for t in tensors], dtype=np.uint64)
+    rc = ips4o_sort_batched(ptrs.ctypes.data, lens.ctypes.data, len(tensors), kt,
+                            _stream_of(tensors[0]) if stream is None else stream)
+    if rc:
+        raise Ips4oError(rc, "ips4o_sort_batched")
+    return tensors
 
 
 def partition(t, key_type="u64", stream: int | None = None):

@@ -111,3 +111,17 @@ def test_log_uniform_lengths():
     assert L.min() >= 16 and L.max() <= 1 << 20
     e = np.log2(L.astype(np.float64))
     assert abs(np.median(e) - 12) < 0.1
+
+
+def test_u64_segments_are_independent_arrays():
+    """Array j of a batch equals the generator run alone on its own length
+    with value seed 1 + 2^32 * j (so TwoDup etc. use the array's length)."""
+    lengths = np.array([5, 0, 17, 1, 64], dtype=np.uint64)
+    for dist in ("uniform", "two_dup", "almost_sorted"):
+        a = inputs.u64_segments(lengths, dist)
+        off = np.concatenate([[0], np.cumsum(lengths)]).astype(int)
+        for j in range(len(lengths)):
+            alone = inputs.u64(int(lengths[j]), dist, seed=1 + (j << 32))
+            assert np.array_equal(a[off[j]:off[j + 1]], alone)
+    b = inputs.u64_segments(lengths[2:], "uniform", first=2)
+    assert np.array_equal(b[:17], inputs.u64(17, "uniform", seed=1 + (2 << 32)))
