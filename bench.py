@@ -10,6 +10,11 @@ than the 129 MB L2, so no flush is needed between steps.
   python bench.py --workload batched [--segments 100000 | --batched-total-log2 28] [--dist two_dup]
       many independent arrays (log-uniform lengths in [16, 2^20]) sorted by
       one ips4o_sort_segmented call per step, against a loop of plain calls
+  python bench.py --workload served [--requests 20000] [--load 0.7]
+      a stream of requests (Poisson arrivals, sizes log-uniform in [2^10, 2^26],
+      u64 : f64 : pair = 2 : 1 : 1, the nine distributions) through the
+      continuous-batching service under a 64 GB HBM budget, against the same
+      stream through one-at-a-time plain calls; p50/p99 latency and keys/s
 
 Prints one JSON line.  `value` is keys/s over all ranks (N > 1 runs
 independent replicas, one per GPU: the sort does not shard).
@@ -490,6 +495,109 @@ def run_batched(args):
     return 0
 
 
+def run_served(args):
+    import torch
+    rank, world, local = _dist_env()
+    if world > 1 and rank != 0:
+        return 0        # the service runs on one GPU; other ranks have no work
+    torch.cuda.set_device(local)
+    from paper_1705_02257_gb300 import build as cuda_build
+    cuda_build.build()
+    from paper_1705_02257_gb300 import inputs, ips4o, serve
+    import oracle
+
+    lo, hi = 10, args.served_max_log2
+    dtypes = {"u64": np.uint64, "f64": np.float64, "pair": inputs.PAIR_DTYPE}
+    # resident inputs: one array of 2^hi elements per (key type, distribution);
+    # a request of n elements of type t and distribution d sorts the first n
+    pools = {}
+    for kt in ("u64", "f64", "pair"):
+        for d in inputs.DISTRIBUTIONS:
+            a = inputs.make(kt, 1 << hi, d)
+            pools[kt, d] = torch.from_numpy(a.view(np.uint8).reshape(-1)).cuda()
+            del a
+    torch.cuda.synchronize()
+    srv = serve.SortServer(budget_bytes=args.budget_gb * 10**9, workers=args.workers,
+                           max_batch_requests=1024, max_batch_keys=1 << 27)
+    sizes, types, dists, unit_arr = inputs.request_stream(args.requests, lo, hi, rate=1.0)
+
+    def make_reqs(rate):
+        return [serve.Request(i, types[i], int(sizes[i]), float(unit_arr[i]) / rate) for i in range(args.requests)]
+
+    def fill(r, buf):
+        buf.copy_(pools[r.key_type, dists[r.rid]][: r.nbytes])
+
+    # calibration: plain one-at-a-time keys/s on the first requests, all
+    # present at time 0; the arrival rate then offers `load` times that
+    calib = [serve.Request(i, types[i], int(sizes[i]), 0.0) for i in range(min(args.requests, 400))]
+    srv.run_one_at_a_time(calib[:50], fill)
+    plain_kps = serve.summarize(srv.run_one_at_a_time(calib, fill))["keys_per_s"]
+
+    rng = np.random.default_rng(7)
+    small = [i for i in range(args.requests) if sizes[i] <= (1 << 22)]
+    sample = set(rng.choice(small, size=min(len(small), args.verify_requests), replace=False).tolist())
+    keep = lambda r: r.rid in sample   # noqa: E731
+    loads = [float(x) for x in str(args.load).split(",")]
+    sweep, oracle_ok, alone_ok, unsorted = [], True, True, []
+    clocks = None
+    for li, load in enumerate(loads):
+        rate = load * plain_kps / float(np.mean(sizes))
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            served = srv.run(make_reqs(rate), fill, keep=keep if li == 0 else (lambda r: False))
+        if li == 0:
+            clocks = clk.summary()
+        plain = srv.run_one_at_a_time(make_reqs(rate), fill, keep=keep if li == 0 else (lambda r: False))
+        s_sum, p_sum = serve.summarize(served), serve.summarize(plain)
+        unsorted += [[load, run, r.rid, r.key_type, r.n, dists[r.rid]] for run, reqs in (("served", served),
+                     ("alone", plain)) for r in reqs if r.sorted_ok is False]
+        sweep.append({"load": load, "arrival_rate_per_s": rate, "served": s_sum, "one_at_a_time": p_sum,
+                      "ratio_keys_per_s": s_sum["keys_per_s"] / p_sum["keys_per_s"],
+                      "ratio_p99": p_sum["p99_ms"] / s_sum["p99_ms"]})
+        if li > 0:
+            continue
+        # each sampled result: the oracle's sort of the input, and the same
+        # as the request sorted alone (one-at-a-time run)
+        for m, a in zip(served, plain):
+            if m.rid not in sample:
+                continue
+            src = pools[m.key_type, dists[m.rid]][: m.nbytes].cpu().numpy().view(dtypes[m.key_type])
+            gm = m.buf.cpu().numpy().view(dtypes[m.key_type])
+            ga = a.buf.cpu().numpy().view(dtypes[m.key_type])
+            exp = oracle.sort(src, m.key_type)
+            if m.key_type == "pair":
+                oracle_ok &= bool(np.array_equal(gm["key"], exp["key"]))
+                alone_ok &= bool(np.array_equal(np.sort(gm, order=["key", "payload"]),
+                                                np.sort(ga, order=["key", "payload"])))
+            else:
+                oracle_ok &= bool(np.array_equal(gm.view(np.uint64), exp.view(np.uint64)))
+                alone_ok &= bool(np.array_equal(gm.view(np.uint64), ga.view(np.uint64)))
+            m.buf = a.buf = None
+    head = sweep[0]
+    peak, peak_kind = _peaks()
+    line = {
+        "metric": METRIC, "value": head["served"]["keys_per_s"], "unit": METRIC, "n_gpus": 1, "steps": 1,
+        "warmup": 1, "ms_per_step": head["served"]["makespan_s"] * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64/f64/pair", "data": "synthetic",
+        "config": {"workload": f"served sort stream: {args.requests} requests, Poisson arrivals at {loads[0]} x "
+                               f"the one-at-a-time keys/s, sizes log-uniform [2^{lo}, 2^{hi}] (seed 4), "
+                               "u64 : f64 : pair = 2 : 1 : 1 and the nine distributions (seed 5), "
+                               f"{args.budget_gb} GB HBM budget, {args.workers} workers",
+                   "requests": args.requests, "keys": head["served"]["keys"],
+                   "l2": "requests resident in HBM; most are larger than L2"},
+        "latency_ms": {k: head["served"][k] for k in ("p50_ms", "p99_ms", "mean_ms", "max_ms")},
+        "vs_one_at_a_time": {"keys_per_s": head["one_at_a_time"]["keys_per_s"],
+                             "p50_ms": head["one_at_a_time"]["p50_ms"], "p99_ms": head["one_at_a_time"]["p99_ms"],
+                             "calibration_keys_per_s": plain_kps},
+        "sweep": sweep,
+        "roofline": None, "cpu_baseline": None, "e2e": None, "clocks": clocks,
+        "gpu_launches": None, "peak_hbm_gbs": peak, "peak_kind": peak_kind,
+        "all_sorted": not unsorted, "unsorted": unsorted[:20],
+        "oracle_sample_ok": oracle_ok, "alone_equals_mixed": alone_ok, "sample_requests": len(sample),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -503,7 +611,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--stripes-per-sm", type=int, default=0, help="override the library's stripes per SM")
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "served"])
+    ap.add_argument("--requests", type=int, default=20_000, help="served: number of requests")
+    ap.add_argument("--load", default="0.7,1.5",
+                    help="served: offered loads (comma-separated), each a multiple of the one-at-a-time keys/s")
+    ap.add_argument("--budget-gb", type=int, default=64, help="served: HBM budget (GB) for requests + workspaces")
+    ap.add_argument("--workers", type=int, default=3, help="served: batches on the device at once")
+    ap.add_argument("--served-max-log2", type=int, default=26, help="served: largest request, 2^x elements")
+    ap.add_argument("--verify-requests", type=int, default=200, help="served: requests checked against the oracle")
     ap.add_argument("--segments", type=int, default=100_000, help="batched: number of arrays")
     ap.add_argument("--batched-total-log2", type=int, default=0,
                     help="batched: draw arrays until this many keys (2^x) instead of --segments")
@@ -513,6 +628,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_gpu(args)
 
 

@@ -187,6 +187,14 @@ ips4o_status ips4o_sort_noalloc(void* d_ptr, size_t n, int key_type, void* strea
 /* Device workspace the library needs for a sort of n elements of the type. */
 size_t ips4o_workspace_bytes(size_t n, int key_type);
 
+/* Make the workspace and host staging of (current device, stream) large
+ * enough for a call on n elements in num_segments segments (1 for
+ * ips4o_sort), so that such calls allocate nothing.  A service reserves its
+ * workers' workspaces up front this way: allocation while other streams run
+ * costs time, and freeing a smaller workspace synchronises the device.
+ * Workspaces only grow; ips4o_release_workspace frees them. */
+ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type, void* stream);
+
 /* Free the workspaces and staging buffers held on the current device (all streams). */
 ips4o_status ips4o_release_workspace(void);
 

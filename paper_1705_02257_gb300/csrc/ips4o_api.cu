@@ -290,6 +290,19 @@ size_t ips4o_workspace_bytes(size_t n, int key_type) {
     }
 }
 
+ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type, void* stream) {
+    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    cudaError_t e;
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    switch (key_type) {
+    case IPS4O_U64: return reserve_u64(*st, n, num_segments);
+    case IPS4O_F64: return reserve_f64(*st, n, num_segments);
+    default: return reserve_pair(*st, n, num_segments);
+    }
+}
+
 ips4o_status ips4o_release_workspace(void) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -536,6 +536,18 @@ ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, Partitio
     return drv.run((typename T::elem_t*)d, (u64)n, part);
 }
 
+// Grow the stream's workspace and staging to what a call on n elements in
+// num_segments segments needs (nothing is freed).
+template <class T>
+ips4o_status reserve_t(DeviceState& st, u64 n, u64 num_segments) {
+    const ips4o_params& prm = global_params();
+    Caps<T> c = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
+    c.init_cap = num_segments;
+    ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, carve<T>(c, nullptr, nullptr));
+    if (rc != IPS4O_OK) return rc;
+    return ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(c));
+}
+
 template <class T>
 ips4o_status sort_segments_t(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s) {
     Driver<T> drv(st, s);

@@ -14,5 +14,8 @@ ips4o_status sort_segments_f64(DeviceState& st, void* d, const std::vector<Task>
 ips4o_status sort_noalloc_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks) {
     return noalloc_sort_t<TF64>(st, d, n, s, tasks);
 }
+ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments) {
+    return reserve_t<TF64>(st, n, num_segments);
+}
 size_t workspace_bytes_f64(size_t n, int sms) { return workspace_bytes_t<TF64>(n, sms); }
 }  // namespace ips4o

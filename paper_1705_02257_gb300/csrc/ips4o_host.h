@@ -54,6 +54,9 @@ constexpr size_t kNoAllocMaxTasks = 256;   // subproblems per level (n / 16Ki <<
 ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
 ips4o_status sort_noalloc_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
 ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
+ips4o_status reserve_u64(DeviceState& st, size_t n, size_t num_segments);
+ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments);
+ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments);
 size_t workspace_bytes_u64(size_t n, int sms);
 size_t workspace_bytes_f64(size_t n, int sms);
 size_t workspace_bytes_pair(size_t n, int sms);

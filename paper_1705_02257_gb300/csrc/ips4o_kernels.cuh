@@ -855,10 +855,18 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
     u32* flags = ws.flags + (u64)j * kMaxBuckets;
     if (threadIdx.x == 0) {
         st_release(&flags[b], 1u);
+        // This bucket's head [Bb, d0 * b) lies in block slot d0 - 1, the last
+        // slot of the region of bucket x, the last bucket before this one
+        // whose region starts below d0 (buckets in between are smaller than a
+        // block and share d0).  Only x's blocks can overshoot into that slot,
+        // so the head may be written once x has read its overshoot.
+        const u32* dl = ws.delim + (u64)j * (kMaxBuckets + 1);
+        int x = (int)b - 1;
+        while (x >= 0 && dl[x] >= d0) --x;
         u32 ok = 1;
-        if (b > 0) {
+        if (x >= 0) {
             u32 it = 0;
-            while (ld_acquire(&flags[b - 1]) == 0) {
+            while (ld_acquire(&flags[x]) == 0) {
                 if (++it > spin_limit) { ok = 0; break; }
                 __nanosleep(32);
             }

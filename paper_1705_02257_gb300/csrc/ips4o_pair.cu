@@ -14,5 +14,8 @@ ips4o_status sort_segments_pair(DeviceState& st, void* d, const std::vector<Task
 ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks) {
     return noalloc_sort_t<TPair>(st, d, n, s, tasks);
 }
+ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments) {
+    return reserve_t<TPair>(st, n, num_segments);
+}
 size_t workspace_bytes_pair(size_t n, int sms) { return workspace_bytes_t<TPair>(n, sms); }
 }  // namespace ips4o

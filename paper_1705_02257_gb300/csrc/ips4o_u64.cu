@@ -14,5 +14,8 @@ ips4o_status sort_segments_u64(DeviceState& st, void* d, const std::vector<Task>
 ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks) {
     return noalloc_sort_t<TU64>(st, d, n, s, tasks);
 }
+ips4o_status reserve_u64(DeviceState& st, size_t n, size_t num_segments) {
+    return reserve_t<TU64>(st, n, num_segments);
+}
 size_t workspace_bytes_u64(size_t n, int sms) { return workspace_bytes_t<TU64>(n, sms); }
 }  // namespace ips4o

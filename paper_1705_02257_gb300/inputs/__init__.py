@@ -67,6 +67,8 @@ def _load():
             lib.gen_pair.argtypes = [u64p, u64, i32, u64, u64]
             lib.gen_rec100.restype = i32
             lib.gen_rec100.argtypes = [u64p, u64, i32, u64, u64]
+            lib.gen_splitmix64_range.restype = i32
+            lib.gen_splitmix64_range.argtypes = [u64p, u64, u64, u64]
             lib.gen_u64_segments.restype = i32
             lib.gen_u64_segments.argtypes = [u64p, u64p, u64, i32, u64, u64]
             lib.gen_log_uniform_lengths.restype = i32
@@ -128,6 +130,18 @@ def log_uniform_lengths(count: int, lo_log2: float, hi_log2: float,
     return out
 
 
+def splitmix64_range(count: int, seed: int, first: int = 0) -> np.ndarray:
+    """Outputs first .. first + count - 1 of the SplitMix64 stream ``seed``."""
+    out = np.empty(count, dtype=np.uint64)
+    _check(_load().gen_splitmix64_range(out.ctypes.data, count, seed, first), "gen_splitmix64_range")
+    return out
+
+
+def unit_uniform(count: int, seed: int, first: int = 0) -> np.ndarray:
+    """Doubles (x >> 11) * 2^-53 in [0, 1) from the SplitMix64 stream ``seed``."""
+    return (splitmix64_range(count, seed, first) >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
 def u64_segments(lengths: np.ndarray, dist: str = "uniform", seed: int = SEED_VALUES, first: int = 0,
                  out: np.ndarray | None = None) -> np.ndarray:
     """Independent arrays back to back: array j has lengths[j] keys of the
@@ -141,6 +155,25 @@ def u64_segments(lengths: np.ndarray, dist: str = "uniform", seed: int = SEED_VA
     _check(_load().gen_u64_segments(out.ctypes.data, lengths.ctypes.data, len(lengths), _dist_id(dist), seed, first),
            "gen_u64_segments")
     return out[:total]
+
+
+REQUEST_TYPES = ("u64", "u64", "f64", "pair")     # drawn uniformly: u64 : f64 : pair = 2 : 1 : 1
+
+
+def request_stream(count: int, lo_log2: float = 10, hi_log2: float = 26, rate: float = 1.0):
+    """The served workload's requests as (sizes, key types, distributions,
+    arrival times in seconds).  Sizes floor(2^U), U ~ U[lo_log2, hi_log2]
+    (seed 4); from the seed-5 stream, draw 3j picks the key type (u64 : f64 :
+    pair = 2 : 1 : 1), draw 3j+1 the distribution (uniform over the nine) and
+    draw 3j+2 the exponential gap before request j (Poisson arrivals at
+    ``rate`` requests per second; request 0 arrives at time 0)."""
+    sizes = log_uniform_lengths(count, lo_log2, hi_log2)
+    u = unit_uniform(3 * count, SEED_ARRIVALS)
+    types = [REQUEST_TYPES[int(x * 4)] for x in u[0::3]]
+    dists = [DISTRIBUTIONS[int(x * len(DISTRIBUTIONS))] for x in u[1::3]]
+    gaps = -np.log1p(-u[2::3]) / rate
+    gaps[0] = 0.0
+    return sizes, types, dists, np.cumsum(gaps)
 
 
 def make(key_type: str, n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:

@@ -279,3 +279,12 @@ int gen_u64_segments(uint64_t* out, const uint64_t* lengths, uint64_t count, int
     free(starts);
     return bad ? -3 : 0;
 }
+
+/* Raw draws of a SplitMix64 stream: out[j] = output (first + j) of the
+ * stream with the given seed (used for request types, distributions and
+ * arrival times of the served workload). */
+int gen_splitmix64_range(uint64_t* out, uint64_t count, uint64_t seed, uint64_t first) {
+    #pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < (int64_t)count; ++j) out[j] = gen_splitmix64_at(seed, first + (uint64_t)j);
+    return 0;
+}

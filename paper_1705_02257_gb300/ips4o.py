@@ -84,6 +84,8 @@ def _load():
                                     ctypes.POINTER(i32)]
     lib.ips4o_workspace_bytes.restype = sz
     lib.ips4o_workspace_bytes.argtypes = [sz, i32]
+    lib.ips4o_reserve_workspace.restype = i32
+    lib.ips4o_reserve_workspace.argtypes = [sz, sz, i32, vp]
     lib.ips4o_release_workspace.restype = i32
     lib.ips4o_release_workspace.argtypes = []
     lib.ips4o_set_params.restype = i32
@@ -148,6 +150,10 @@ def ips4o_partition(d_ptr: int, n: int, key_type: int, stream: int = 0):
 
 def ips4o_workspace_bytes(n: int, key_type: int) -> int:
     return int(_lib.ips4o_workspace_bytes(n, key_type))
+
+
+def ips4o_reserve_workspace(n: int, num_segments: int, key_type: int, stream: int = 0) -> int:
+    return _lib.ips4o_reserve_workspace(n, num_segments, key_type, stream)
 
 
 def ips4o_release_workspace() -> int:

@@ -163,6 +163,7 @@ def test_ones_single_equality_bucket(ips4o):
 
 
 def test_stats_counters(ips4o):
+    ips4o.ips4o_release_workspace()     # the workspace is then sized for this call alone
     a = inputs.u64(1 << 22)
     t = torch.from_numpy(a.view(np.int64).copy()).cuda()
     ips4o.sort(t, "u64")
@@ -197,3 +198,30 @@ def test_deep_recursion(ips4o, dist, k_max, bcm):
             assert ips4o.stats()["levels"] >= 2
     finally:
         ips4o.reset_params()
+
+
+@pytest.mark.parametrize("kt,n", [("u64", 45_312_840), ("pair", 19_488_133)])
+def test_heavy_duplicates_repeated(ips4o, kt, n):
+    """RootDup keys (the first n of a 2^26-element RootDup array: 8192 keys,
+    each about n / 8192 times) make equality buckets (Section 4.4), with
+    empty buckets between non-empty ones, so the last block of a bucket can
+    overshoot across empty buckets into the head of the next non-empty one
+    (Section 4.3).  The head may only be written after the overshoot has
+    been read; a wrong hand-off is a race, so the sort is repeated and every
+    result compared with the oracle's."""
+    a = inputs.make(kt, 1 << 26, "root_dup")[:n].copy()
+    exp = oracle.sort(a, kt)
+    exp_keys = exp["key"] if kt == "pair" else exp
+    d_exp = torch.from_numpy(exp_keys.view(np.int64).copy()).cuda()
+    src = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1).copy()).cuda()
+    work = torch.empty_like(src)
+    for it in range(30):
+        work.copy_(src)
+        ips4o.sort(work, kt)
+        keys = work.view(torch.int64)
+        if kt == "pair":
+            keys = keys.view(-1, 2)[:, 0]
+        assert torch.equal(keys, d_exp), f"iteration {it}"
+    if kt == "pair":
+        got = work.cpu().numpy().view(inputs.PAIR_DTYPE)
+        assert oracle.multiset_hash(got, kt) == oracle.multiset_hash(a, kt)

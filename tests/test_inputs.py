@@ -125,3 +125,21 @@ def test_u64_segments_are_independent_arrays():
             assert np.array_equal(a[off[j]:off[j + 1]], alone)
     b = inputs.u64_segments(lengths[2:], "uniform", first=2)
     assert np.array_equal(b[:17], inputs.u64(17, "uniform", seed=1 + (2 << 32)))
+
+
+def test_splitmix64_range_matches_single_draws():
+    r = inputs.splitmix64_range(5, 5, first=3)
+    assert [int(x) for x in r] == [inputs.splitmix64_at(5, 3 + j) for j in range(5)]
+    u = inputs.unit_uniform(1000, 5)
+    assert u.min() >= 0.0 and u.max() < 1.0
+
+
+def test_request_stream_mix_and_rate():
+    sizes, types, dists, arr = inputs.request_stream(20000, 10, 26, rate=100.0)
+    assert sizes.min() >= 1024 and sizes.max() <= 1 << 26
+    frac = {t: types.count(t) / len(types) for t in ("u64", "f64", "pair")}
+    assert abs(frac["u64"] - 0.5) < 0.02 and abs(frac["f64"] - 0.25) < 0.02 and abs(frac["pair"] - 0.25) < 0.02
+    assert set(dists) == set(inputs.DISTRIBUTIONS)
+    assert arr[0] == 0.0 and np.all(np.diff(arr) >= 0)
+    # Poisson process: mean gap 1 / rate
+    assert abs(np.diff(arr).mean() - 0.01) < 0.0005
