@@ -36,6 +36,33 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "keys/s"
+ELEM_BYTES = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+DTYPE_NAME = {"u64": "u64", "f64": "f64", "pair": "u64 key + u64 payload", "rec100": "80-bit byte key + 90-byte payload"}
+KT_LABEL = {"u64": "uint64 keys", "f64": "float64 keys", "pair": "16-byte (uint64 key, uint64 payload) pairs",
+            "rec100": "100-byte records (10-byte key)"}
+
+
+def _sorted_keys(t, kt) -> bool:
+    """Keys non-decreasing in the library's order, checked on the device."""
+    import torch
+    if kt == "rec100":
+        r = t.view(-1, 100)
+        b = r[:, :10].to(torch.int64)
+        hi = torch.zeros(r.shape[0], dtype=torch.int64, device=t.device)
+        for q in range(7):                      # the first 7 bytes fit a signed 64-bit compare
+            hi = hi * 256 + b[:, q]
+        lo = (b[:, 7] << 16) | (b[:, 8] << 8) | b[:, 9]
+        d_hi = hi[1:] - hi[:-1]
+        ok = (d_hi > 0) | ((d_hi == 0) & (lo[1:] >= lo[:-1]))
+        return bool(ok.all().item())
+    if kt == "f64":
+        x = t.view(torch.float64)
+    else:
+        x = t.view(torch.int64)
+        if kt == "pair":
+            x = x.view(-1, 2)[:, 0]
+        x = x ^ (-(1 << 63))
+    return bool((x[1:] >= x[:-1]).all().item())
 LOG2N = 28
 FALLBACK_HBM_GBS = 6800.0
 
@@ -118,19 +145,19 @@ class ClockSampler:
         return out
 
 
-def cpu_baseline(log2n_sample: int = 24, reps: int = 1):
+def cpu_baseline(log2n_sample: int = 24, reps: int = 1, kt: str = "u64", dist: str = "uniform"):
     """The oracle, as it stands, single-threaded on a bounded sample."""
     import oracle
     from paper_1705_02257_gb300 import inputs
     n = 1 << log2n_sample
-    a = inputs.u64(n, "uniform")
-    oracle.sort(a[:1024], "u64")                      # load/build outside the timing
+    a = inputs.make(kt, n, dist)
+    oracle.sort(a[:1024], kt)                         # load/build outside the timing
     t0 = time.perf_counter()
     for _ in range(reps):
-        oracle.sort(a, "u64")
+        oracle.sort(a, kt)
     dt = time.perf_counter() - t0
     return {"value": n * reps / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"2^{log2n_sample} uint64 Uniform keys (seed 1), {reps} sort(s), single-threaded C oracle, "
+            "sample": f"2^{log2n_sample} {KT_LABEL[kt]}, {dist} (seed 1), {reps} sort(s), single-threaded C oracle, "
                       f"{dt:.1f} s", "host_cores": os.cpu_count()}
 
 
@@ -140,29 +167,30 @@ def run_reference(args):
         return 0
     import oracle
     from paper_1705_02257_gb300 import inputs
-    log2s = args.ref_log2n
+    kt = args.key_type
+    log2s = min(args.ref_log2n, 20) if kt == "rec100" else args.ref_log2n
     n = 1 << log2s
-    base = inputs.u64(n, args.dist)
-    oracle.sort(base[:1024], "u64")
+    base = inputs.make(kt, n, args.dist)
+    oracle.sort(base[:1024], kt)
     for _ in range(args.warmup):
-        oracle.sort(base, "u64")
+        oracle.sort(base, kt)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sort(base, "u64")
+        oracle.sort(base, kt)
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = n * args.steps / total
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[kt], "data": "synthetic",
         "impl": "reference",
-        "config": {"workload": f"in-place sort of 2^{LOG2N} uint64 keys, {args.dist} (seed 1); "
-                               f"reference steps sort a 2^{log2s}-key sample",
-                   "n": 1 << LOG2N, "key_type": "u64", "distribution": args.dist},
+        "config": {"workload": f"{'sort' if kt == 'rec100' else 'in-place sort'} of 2^{args.log2n} {KT_LABEL[kt]}, "
+                               f"{args.dist} (seed 1); reference steps sort a 2^{log2s}-element sample",
+                   "n": 1 << args.log2n, "key_type": kt, "distribution": args.dist},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": f"2^{log2s} uint64 {args.dist} keys per step, single-threaded C oracle"},
+                         "sample": f"2^{log2s} {KT_LABEL[kt]}, {args.dist}, per step, single-threaded C oracle"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -182,8 +210,10 @@ def run_gpu(args):
     from paper_1705_02257_gb300 import inputs, ips4o
 
     n = 1 << args.log2n
-    host = inputs.u64(n, args.dist)
-    pristine = torch.from_numpy(host.view(np.int64)).cuda()
+    kt = args.key_type
+    host = inputs.make(kt, n, args.dist)
+    elem = ELEM_BYTES[kt]
+    pristine = torch.from_numpy(np.ascontiguousarray(host).view(np.uint8).reshape(-1)).cuda()
     work = torch.empty_like(pristine)
     stream = torch.cuda.current_stream()
     ips4o.reset_params()
@@ -197,7 +227,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        ips4o.sort(work, "u64")
+        ips4o.sort(work, kt)
         e.record(stream)
         torch.cuda.synchronize()
         return s.elapsed_time(e)
@@ -225,8 +255,7 @@ def run_gpu(args):
     levels = stats["levels"]
 
     # output check on the last timed step: sorted and a permutation
-    out = work.cpu().numpy().view(np.uint64)
-    sorted_ok = bool(np.all(out[1:] >= out[:-1]))
+    sorted_ok = _sorted_keys(work, kt)
 
     # per-kernel times (CUDA events around each launch on the sort's stream)
     ips4o.set_params(profile=1, **base_params)
@@ -242,33 +271,38 @@ def run_gpu(args):
     ips4o.reset_params()
     if base_params:
         ips4o.set_params(**base_params)
-    elem = 8
     # algorithmic bytes per launch (Appendix B I/O volume): classification and
     # block permutation each read and write the elements of the launch once.
-    per_level = 2.0 * n * elem * levels * prof_steps
+    # Records are distributed as 16-byte (key prefix, index) pairs.
+    dist_elem = 16 if kt == "rec100" else elem
+    per_level = 2.0 * n * dist_elem * levels * prof_steps
     alg = {
         "classify": per_level,
         "block_permutation": per_level,
-        "cleanup_base_case": 2.0 * n * elem * prof_steps,
+        "cleanup_base_case": 2.0 * n * dist_elem * prof_steps,
     }
     dominant = max(alg, key=lambda p: phase_ms[p])
     peak, peak_kind = _peaks()
     achieved = alg[dominant] / (phase_ms[dominant] * 1e-3) / 1e9 if phase_ms[dominant] > 0 else None
     ms_per_step = total_ms / args.steps
     value = n * world * args.steps / (total_ms * 1e-3)
-    alg_sort = (4 * levels + 2) * n * elem
+    alg_sort = (4 * levels + 2) * n * dist_elem
+    if kt == "rec100":
+        # key extraction (12 bytes read, 16 written), input copy (read + write)
+        # and the gather (pair read, record read + write)
+        alg_sort += n * (12 + 16) + 2 * n * elem + n * (16 + 2 * elem)
     sort_frac = alg_sort / (ms_per_step * 1e-3) / 1e9 / peak
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
     if not args.no_e2e:
-        h_in = torch.from_numpy(host.view(np.int64)).pin_memory()
+        h_in = torch.from_numpy(np.ascontiguousarray(host).view(np.uint8).reshape(-1)).pin_memory()
         h_work = torch.empty_like(h_in).pin_memory()
         e2e_times = []
         for i in range(args.warmup + args.steps):
             h_work.copy_(h_in)
             t0 = time.perf_counter()
-            rc = ips4o.ips4o_sort_host(h_work.data_ptr(), n, ips4o.U64, stream.cuda_stream)
+            rc = ips4o.ips4o_sort_host(h_work.data_ptr(), n, ips4o.KEY_TYPES[kt], stream.cuda_stream)
             dt = time.perf_counter() - t0
             if rc:
                 raise ips4o.Ips4oError(rc, "ips4o_sort_host")
@@ -287,15 +321,17 @@ def run_gpu(args):
         if dist_on:
             tdist.destroy_process_group()
         return 0
-    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(args.cpu_log2n)
+    cpu = None if args.no_cpu_baseline or world > 1 else cpu_baseline(
+        min(args.cpu_log2n, 22) if kt == "rec100" else args.cpu_log2n, kt=kt, dist=args.dist)
     clocks = clk.summary()
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": f"in-place sort of 2^{args.log2n} uint64 keys, {args.dist} (seed 1)",
-                   "n": n, "key_type": "u64", "distribution": args.dist,
-                   "l2": "input 2 GiB per step, larger than the 129 MB L2 (no flush needed)",
+        "vs_baseline": None, "dtype": DTYPE_NAME[kt], "data": "synthetic",
+        "config": {"workload": f"{'sort' if kt == 'rec100' else 'in-place sort'} of 2^{args.log2n} {KT_LABEL[kt]}, "
+                               f"{args.dist} (seed 1)",
+                   "n": n, "key_type": kt, "distribution": args.dist,
+                   "l2": f"input {n * elem / 2**30:.2f} GiB per step, larger than the 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}", "levels": levels},
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
@@ -606,6 +642,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--log2n", type=int, default=LOG2N)
+    ap.add_argument("--key-type", default="u64", choices=["u64", "f64", "pair", "rec100"],
+                    help="plain workload: element type (f64 and pair at 2^27, rec100 at 2^24 in the paper's table)")
     ap.add_argument("--ref-log2n", type=int, default=22)
     ap.add_argument("--cpu-log2n", type=int, default=24)
     ap.add_argument("--no-e2e", action="store_true")

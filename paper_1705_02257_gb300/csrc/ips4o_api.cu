@@ -101,9 +101,12 @@ static size_t elem_size(int kt) {
     case IPS4O_U64: return 8;
     case IPS4O_F64: return 8;
     case IPS4O_PAIR_U64: return 16;
+    case IPS4O_REC100_K10: return 100;
     default: return 0;
     }
 }
+
+static size_t elem_align(int kt) { return kt == IPS4O_REC100_K10 ? 4 : elem_size(kt); }
 
 static ips4o_status check_args(const void* p, size_t n, int kt) {
     if (kt < 0 || kt > IPS4O_REC100_K10) return IPS4O_ERR_UNSUPPORTED_TYPE;
@@ -112,7 +115,7 @@ static ips4o_status check_args(const void* p, size_t n, int kt) {
     // one bucket region of the block permutation holds at most 2^25 - 2^16 - 2
     // blocks of 512 bytes (the packed pointer word): 16 GiB per call
     if (n > ((size_t)16 << 30) / elem_size(kt)) return IPS4O_ERR_TOO_LARGE;
-    if (p && ((uintptr_t)p % elem_size(kt)) != 0) return IPS4O_ERR_MISALIGNED;
+    if (p && ((uintptr_t)p % elem_align(kt)) != 0) return IPS4O_ERR_MISALIGNED;
     return IPS4O_OK;
 }
 
@@ -122,6 +125,10 @@ static ips4o_status dispatch(DeviceState& st, void* d, size_t n, int kt, cudaStr
     case IPS4O_U64: rc = sort_u64(st, d, n, s, part); break;
     case IPS4O_F64: rc = sort_f64(st, d, n, s, part); break;
     case IPS4O_PAIR_U64: rc = sort_pair(st, d, n, s, part); break;
+    case IPS4O_REC100_K10:
+        if (part) return IPS4O_ERR_UNSUPPORTED_TYPE;   // records are sorted through key + index pairs
+        rc = sort_rec100(st, d, n, s);
+        break;
     default: return IPS4O_ERR_UNSUPPORTED_TYPE;
     }
     publish_stats(st);
@@ -286,6 +293,7 @@ size_t ips4o_workspace_bytes(size_t n, int key_type) {
     case IPS4O_U64: return workspace_bytes_u64(n, sms);
     case IPS4O_F64: return workspace_bytes_f64(n, sms);
     case IPS4O_PAIR_U64: return workspace_bytes_pair(n, sms);
+    case IPS4O_REC100_K10: return workspace_bytes_pair(n, sms) + rec100_aux_bytes(n);
     default: return 0;
     }
 }
@@ -299,7 +307,11 @@ ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type
     switch (key_type) {
     case IPS4O_U64: return reserve_u64(*st, n, num_segments);
     case IPS4O_F64: return reserve_f64(*st, n, num_segments);
-    default: return reserve_pair(*st, n, num_segments);
+    case IPS4O_PAIR_U64: return reserve_pair(*st, n, num_segments);
+    default: {
+        ips4o_status rc = reserve_pair(*st, n, num_segments);
+        return rc != IPS4O_OK ? rc : ensure_device_buffer(&st->d_aux, &st->aux_bytes, rec100_aux_bytes(n));
+    }
     }
 }
 
@@ -317,11 +329,12 @@ ips4o_status ips4o_release_workspace(void) {
         std::lock_guard<std::mutex> lk(st->mtx);
         if (st->d_ws) cudaFree(st->d_ws);
         if (st->d_host_copy) cudaFree(st->d_host_copy);
+        if (st->d_aux) cudaFree(st->d_aux);
         if (st->h_stage) cudaFreeHost(st->h_stage);
         for (cudaEvent_t ev : st->events) cudaEventDestroy(ev);
         st->events.clear();
-        st->d_ws = st->d_host_copy = st->h_stage = nullptr;
-        st->ws_bytes = st->d_host_copy_bytes = st->h_stage_bytes = 0;
+        st->d_ws = st->d_host_copy = st->d_aux = st->h_stage = nullptr;
+        st->ws_bytes = st->d_host_copy_bytes = st->aux_bytes = st->h_stage_bytes = 0;
     }
     return IPS4O_OK;
 }

@@ -97,11 +97,13 @@ struct BaseCfg {
     static constexpr int EPT = CAP / TPB;
     static constexpr int N0 = 2;             // target sub-bucket size
     static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
-    static constexpr int LIMIT = 64;         // any larger sub-bucket: whole-bucket bitonic fallback
+    static constexpr int LIMIT = 64;         // larger sub-buckets are sorted one at a time by the CTA
+    static constexpr int MAXBIG = CAP / LIMIT;
     static constexpr size_t off_data = 0;
     static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[MAXSUB + 1]
     static constexpr size_t off_tmp = off_off + (MAXSUB + 1) * 4 + 12;
-    static constexpr size_t smem_bytes = off_tmp + 64 * 8;
+    static constexpr size_t off_big = off_tmp + 64 * 8;                     // u32[MAXBIG + 1]
+    static constexpr size_t smem_bytes = off_big + (MAXBIG + 1) * 4;
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
     static_assert(CAP <= 65535, "ranks are packed in 16 bits");
@@ -158,9 +160,10 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 // counting-sort scatter into shared memory, each element's final position is
 // the start of its sub-bucket plus the number of keys of that sub-bucket
 // that are smaller (or equal and earlier), and it is written there directly.
-// If some sub-bucket exceeds LIMIT elements (clustered keys), the whole
-// bucket is sorted by a bitonic network instead, so the cost stays bounded
-// for any input.
+// Sub-buckets of more than LIMIT elements (clustered or repeated keys) are
+// handled afterwards, one at a time by the whole CTA: left as they are when
+// all their keys are equal, else sorted in shared memory by a bitonic
+// network, so the cost stays bounded for any input.
 template <class T, class C>
 __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     typedef typename T::elem_t E;
@@ -170,6 +173,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     E* data = (E*)(smem + C::off_data);
     u32* off = (u32*)(smem + C::off_off);          // sub-bucket sizes, then (scanned) starts
     u64* tmp = (u64*)(smem + C::off_tmp);
+    u32* big_list = (u32*)(smem + C::off_big);     // [0] count, then the large sub-buckets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     E e[EPT];
@@ -186,7 +190,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     }
 #pragma unroll
     for (int q = 0; q < SPT; ++q) off[tid * SPT + q] = 0;
-    if (tid == 0) off[C::MAXSUB] = 0;
+    if (tid == 0) { off[C::MAXSUB] = 0; big_list[0] = 0; }
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -233,14 +237,14 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     __syncthreads();
     // exclusive scan of the sub-bucket sizes in place (SPT consecutive entries
     // per thread); off[MAXSUB] receives the total
-    u32 c[SPT], csum = 0, cmax = 0;
+    u32 c[SPT], csum = 0;
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
         c[q] = off[tid * SPT + q];
         csum += c[q];
-        cmax = c[q] > cmax ? c[q] : cmax;
+        if (c[q] > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = tid * SPT + q;
     }
-    const int big = __syncthreads_or(cmax > (u32)C::LIMIT ? 1 : 0);
+    __syncthreads();
     u32 tot;
     u32 pre = block_exclusive_scan<u32>(csum, (u32*)tmp, &tot);
 #pragma unroll
@@ -259,32 +263,36 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         }
     }
     __syncthreads();
-    if (big) {
-        // clustered keys: sort the whole bucket with a bitonic network
-        cta_bitonic<T, TPB>(data, m);
+    // final position = sub-bucket start + rank of the key within it
+    // (elements of large sub-buckets are placed below)
 #pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const u32 idx = tid + q * TPB;
-            if (idx < m) g[idx] = data[idx];
-        }
-    } else {
-        // final position = sub-bucket start + rank of the key within it
-#pragma unroll
-        for (int q = 0; q < EPT; ++q) {
-            const u32 i = tid + q * TPB;
-            if (i < m) {
-                const E x = data[i];
-                const K k = T::key(x);
-                const u32 sb = sub_of(k);
-                const u32 o = off[sb], o1 = off[sb + 1];
-                u32 r = 0;
-                for (u32 jj = o; jj < o1; ++jj) {
-                    const K kj = T::key(data[jj]);
-                    r += (kj < k || (kj == k && jj < i)) ? 1u : 0u;
-                }
-                g[o + r] = x;
+    for (int q = 0; q < EPT; ++q) {
+        const u32 i = tid + q * TPB;
+        if (i < m) {
+            const E x = data[i];
+            const K k = T::key(x);
+            const u32 sb = sub_of(k);
+            const u32 o = off[sb], o1 = off[sb + 1];
+            if (o1 - o > (u32)C::LIMIT) continue;
+            u32 r = 0;
+            for (u32 jj = o; jj < o1; ++jj) {
+                const K kj = T::key(data[jj]);
+                r += (kj < k || (kj == k && jj < i)) ? 1u : 0u;
             }
+            g[o + r] = x;
         }
+    }
+    const u32 nbig = big_list[0];
+    for (u32 q = 0; q < nbig; ++q) {
+        const u32 sb = big_list[1 + q];
+        const u32 o = off[sb], len = off[sb + 1] - o;
+        // all keys equal: any order is sorted
+        const K k0 = T::key(data[o]);
+        int differs = 0;
+        for (u32 i = tid; i < len; i += TPB) differs |= T::key(data[o + i]) != k0;
+        if (__syncthreads_or(differs)) cta_bitonic<T, TPB>(data + o, len);
+        for (u32 i = tid; i < len; i += TPB) g[o + i] = data[o + i];
+        __syncthreads();
     }
     __syncthreads();
 }

@@ -20,6 +20,8 @@ struct DeviceState {
     size_t h_stage_bytes = 0;
     void* d_host_copy = nullptr;    // device buffer for ips4o_sort_host
     size_t d_host_copy_bytes = 0;
+    void* d_aux = nullptr;          // 100-byte records: pairs, input copy, run bounds
+    size_t aux_bytes = 0;
     std::vector<cudaEvent_t> events;
     std::mutex mtx;
     ips4o_stats stats{};
@@ -57,6 +59,8 @@ ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t 
 ips4o_status reserve_u64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments);
+ips4o_status sort_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s);
+size_t rec100_aux_bytes(size_t n);
 size_t workspace_bytes_u64(size_t n, int sms);
 size_t workspace_bytes_f64(size_t n, int sms);
 size_t workspace_bytes_pair(size_t n, int sms);

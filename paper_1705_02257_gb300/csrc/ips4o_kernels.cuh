@@ -406,6 +406,11 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
         s_delim[nb] = (u32)ceil_div(sub.n, B);
     }
     __syncthreads();
+    // a subproblem whose elements all fall into one bucket (e.g. all keys
+    // equal): every full block already lies in that bucket's region, so the
+    // block permutation has nothing to move
+    const bool single = __syncthreads_or((u32)b < nb && c == sub.n) != 0;
+    bool no_blocks = true;
     if ((u32)b < nb) {
         const u32 d0 = s_delim[b], d1 = s_delim[b + 1];
         u32 nfr = 0;
@@ -421,9 +426,13 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
         }
         const u32 holes = nfr - in_zone;
         delim[b] = d0;
-        // w_i = d_i, r_i = d_i + nfr - 1 (the last full block of the region), no readers
+        // w_i = d_i, r_i = d_i + nfr - 1 (the last full block of the region), no
+        // readers; with a single non-empty bucket, w_i = d_i + nfr: its blocks
+        // count as already written in place
         if ((u64)(d1 - d0) > kMaxRegionBlocks) set_status(ws.ctr, kStatusCapacity);
-        ws.wr[(u64)j * kMaxBuckets + b] = (u64)((long long)nfr - 1 + (long long)kRBias) << kRdBits;
+        const u64 w0 = single ? (u64)nfr << kWShift : 0ull;
+        ws.wr[(u64)j * kMaxBuckets + b] = w0 | ((u64)((long long)nfr - 1 + (long long)kRBias) << kRdBits);
+        no_blocks = single || nfr == 0;
         ws.flags[(u64)j * kMaxBuckets + b] = 0;
         ws.region_full[(u64)j * kMaxBuckets + b] = nfr;
         ws.bucket_full[(u64)j * kMaxBuckets + b] = fb;
@@ -434,13 +443,10 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
         }
     }
     if (b == 0) delim[nb] = s_delim[nb];
-    if (b < 8) {
-        // buckets beyond nb never hold blocks: mark them exhausted
-        u32 word = 0;
-        for (int q = 0; q < 32; ++q)
-            if ((u32)(b * 32 + q) >= nb) word |= 1u << q;
-        ws.exhausted[(u64)j * 8 + b] = word;
-    }
+    // buckets without unprocessed blocks (beyond nb, no full block in the
+    // region, or all in place) start out exhausted: no mover probes them
+    const u32 word = __ballot_sync(0xffffffffu, no_blocks);
+    if ((b & 31) == 0) ws.exhausted[(u64)j * 8 + (b >> 5)] = word;
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < ns; ++i) blocks += s_full[i];
         ws.subs[j].blocks_total = blocks;

@@ -42,6 +42,7 @@ def test_argument_errors_without_device_work(lib):
     assert ips4o.ips4o_sort(0, 10, ips4o.U64, 0) == 1          # null pointer, n > 0
     assert ips4o.ips4o_sort(0, 10, 17, 0) == 2                  # unknown key type
     assert ips4o.ips4o_sort(8 * 1024 + 4, 10, ips4o.U64, 0) == 3  # misaligned
+    assert ips4o.ips4o_sort(8 * 1024 + 2, 10, ips4o.REC100_K10, 0) == 3   # records: 4-byte alignment
     assert ips4o.ips4o_sort(0, 0, ips4o.U64, 0) == 0            # empty input: no-op
     assert ips4o.ips4o_sort(0, 1, ips4o.U64, 0) == 0
     assert ips4o.ips4o_status_string(6) == "bounded device wait timed out"
