@@ -407,6 +407,8 @@ def run_batched(args):
         j = j1
     stream = torch.cuda.current_stream()
     ips4o.reset_params()
+    if args.segment_scheduler:
+        ips4o.set_params(segment_scheduler=args.segment_scheduler)
     off_host = np.ascontiguousarray(off)
 
     def one_step():
@@ -510,7 +512,8 @@ def run_batched(args):
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"batched segmented sort: {label}, log-uniform lengths [16, 2^20] (seed 4), "
-                               f"{args.dist} keys per array, one ips4o_sort_segmented call",
+                               f"{args.dist} keys per array, one ips4o_sort_segmented call "
+                               f"({['automatic', 'level by level', 'segment scheduler'][args.segment_scheduler]})",
                    "segments": nseg, "n": total, "key_type": "u64", "distribution": args.dist,
                    "l2": f"{total * 8 / 2**30:.1f} GiB per step, larger than L2",
                    "parallelism": f"replicas x{world}"},
@@ -661,6 +664,8 @@ def main():
     ap.add_argument("--batched-total-log2", type=int, default=0,
                     help="batched: draw arrays until this many keys (2^x) instead of --segments")
     ap.add_argument("--verify-segments", type=int, default=200, help="batched: arrays checked against the oracle")
+    ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2],
+                    help="batched: 0 automatic, 1 level by level, 2 one CTA per array")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -87,6 +87,10 @@ typedef struct {
     int stripes_per_sm;   /* stripes (local-classification work items) per SM for a level; default 2 */
     int profile;          /* 1: time every kernel with CUDA events into ips4o_stats.phase_ms */
     uint64_t seed;        /* sampling seed */
+    int segment_scheduler;  /* ips4o_sort_segmented / ips4o_sort_batched: 0 automatic (currently
+                               level by level, the faster of the two), 1 level by level across
+                               all segments, 2 the segment scheduler (one CTA per array, as in
+                               ips4o_sort_segmented_async) */
 } ips4o_params;
 
 /* Counters of the last completed call on the calling thread's current device. */
@@ -155,6 +159,26 @@ ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream,
 ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t num_segments, int key_type,
                                   void* stream);
 
+/* ips4o_sort_segmented without any host work after the call returns:
+ * d_offsets (num_segments + 1 element indices) must be in DEVICE memory, the
+ * call only enqueues kernels on `stream` (it neither allocates, nor copies
+ * to or from the host, nor synchronises), so it can be captured into a CUDA
+ * graph and replayed.  The arrays are sorted by the segment scheduler: one
+ * persistent launch in which each CTA sorts whole arrays (the distribution
+ * steps and the base case of one array by one CTA), largest arrays first,
+ * after three small kernels that build that queue on the device.
+ *   - The workspace of (current device, stream) must have been reserved
+ *     with ips4o_reserve_workspace(n >= 1, num_segments, key_type, stream);
+ *     otherwise IPS4O_ERR_TOO_LARGE is returned and nothing is enqueued.
+ *   - Device-side errors (decreasing offsets, a bounded wait that gave up,
+ *     a broken invariant) are recorded in the stream's status word:
+ *     ips4o_stream_status(stream) waits for the stream and returns them.
+ *   - ips4o_get_stats does not report these calls.  u64, f64 and pair only.
+ * Segments of any length are sorted; each runs on one SM, so arrays much
+ * longer than 2^22 elements are better served by ips4o_sort_segmented. */
+ips4o_status ips4o_sort_segmented_async(void* d_base, const uint64_t* d_offsets, size_t num_segments,
+                                        int key_type, void* stream);
+
 /* Sort `count` separate device arrays, ptrs[i][0 .. lens[i]), each in place,
  * in one call (the same processing as ips4o_sort_segmented).  ptrs and lens
  * are arrays of `count` entries in host or device memory; every ptrs[i] with
@@ -165,8 +189,10 @@ ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t 
                                 void* stream);
 
 /* Waits for all work on `stream` and reports a CUDA error that it raised
- * (IPS4O_ERR_CUDA, text in ips4o_last_cuda_error), else IPS4O_OK.  The sort
- * calls already return device-side errors themselves. */
+ * (IPS4O_ERR_CUDA, text in ips4o_last_cuda_error), then the device status
+ * word of the last ips4o_sort_segmented_async call on the stream
+ * (IPS4O_ERR_TIMEOUT, IPS4O_ERR_INTERNAL), else IPS4O_OK.  The other sort
+ * calls return device-side errors themselves. */
 ips4o_status ips4o_stream_status(void* stream);
 
 /* Sort d_ptr[0..n) in place, like ips4o_sort, without allocating any memory.

@@ -23,7 +23,7 @@ std::mutex g_mtx;
 // different streams run side by side, calls on one stream are serialised
 std::map<std::pair<int, uintptr_t>, DeviceState*> g_states;
 ips4o_stats g_last_stats[64];
-ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
+ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0};
 thread_local char g_last_err[256] = {0};
 }  // namespace
 
@@ -213,6 +213,25 @@ ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t 
     return dispatch_segments(*st, d_base, segs, key_type, (cudaStream_t)stream);
 }
 
+ips4o_status ips4o_sort_segmented_async(void* d_base, const uint64_t* d_offsets, size_t num_segments, int key_type,
+                                        void* stream) {
+    if (key_type < 0 || key_type > IPS4O_PAIR_U64) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (num_segments == 0) return IPS4O_OK;
+    if (!d_offsets || !d_base) return IPS4O_ERR_INVALID_ARG;
+    if (((uintptr_t)d_base % elem_align(key_type)) != 0) return IPS4O_ERR_MISALIGNED;
+    if (num_segments >= (1ull << 32)) return IPS4O_ERR_TOO_LARGE;
+    cudaError_t e;
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (key_type) {
+    case IPS4O_U64: return enqueue_segments_u64(*st, d_base, d_offsets, num_segments, s);
+    case IPS4O_F64: return enqueue_segments_f64(*st, d_base, d_offsets, num_segments, s);
+    default: return enqueue_segments_pair(*st, d_base, d_offsets, num_segments, s);
+    }
+}
+
 ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t count, int key_type, void* stream) {
     if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (count == 0) return IPS4O_OK;
@@ -334,6 +353,7 @@ ips4o_status ips4o_release_workspace(void) {
         for (cudaEvent_t ev : st->events) cudaEventDestroy(ev);
         st->events.clear();
         st->d_ws = st->d_host_copy = st->d_aux = st->h_stage = nullptr;
+        st->d_status = nullptr;
         st->ws_bytes = st->d_host_copy_bytes = st->aux_bytes = st->h_stage_bytes = 0;
     }
     return IPS4O_OK;
@@ -342,12 +362,13 @@ ips4o_status ips4o_release_workspace(void) {
 ips4o_status ips4o_set_params(const ips4o_params* p) {
     std::lock_guard<std::mutex> lk(g_mtx);
     if (!p) {
-        g_params = ips4o_params{256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
+        g_params = ips4o_params{256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0};
         return IPS4O_OK;
     }
     if (p->k_max < 4 || p->k_max > 256 || (p->k_max & (p->k_max - 1)) != 0) return IPS4O_ERR_INVALID_ARG;
     if (p->stripes_per_sm < 1 || p->stripes_per_sm > 16) return IPS4O_ERR_INVALID_ARG;
     if (p->alpha > 4095) return IPS4O_ERR_INVALID_ARG;
+    if (p->segment_scheduler < 0 || p->segment_scheduler > 2) return IPS4O_ERR_INVALID_ARG;
     g_params = *p;
     return IPS4O_OK;
 }
@@ -400,6 +421,15 @@ ips4o_status ips4o_stream_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) { set_last_cuda_error(e, "ips4o_stream_status"); return IPS4O_ERR_CUDA; }
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    if (!st->d_status) return IPS4O_OK;
+    unsigned bits = 0;
+    e = cudaMemcpy(&bits, st->d_status, sizeof bits, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "ips4o_stream_status"); return IPS4O_ERR_CUDA; }
+    if (bits & 1u) return IPS4O_ERR_TIMEOUT;
+    if (bits) return IPS4O_ERR_INTERNAL;
     return IPS4O_OK;
 }
 

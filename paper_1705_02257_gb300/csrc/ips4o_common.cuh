@@ -164,11 +164,13 @@ struct Workspace {
     Task* next_tasks;         // [next_cap]
     Task* base_small;         // [max_sub * 256] buckets for the small base case
     Task* base_large;         // [max_sub * 256] buckets for the large base case
-    Task* init_tasks;         // [init_cap]      segments sorted by the base case alone
-    u32* init_count;          // [2]             small / large entries of init_tasks
+    Task* init_tasks;         // [init_cap]      segments sorted by the base case alone / scheduler queue
+    u32* init_count;          // [2]             small / large entries of init_tasks; queue length, cursor
+    u32* hist;                // [65]            scheduler queue built on the device: size groups
+    Task* stacks;             // [max_sub][stack_cap] scheduler: buckets each CTA still has to distribute
     ChunkCounters* ctr;       // [1]
     u32 max_sub, max_stripes;
-    u64 pool_cap, next_cap, init_cap;
+    u64 pool_cap, next_cap, init_cap, stack_cap;
 };
 
 // ------------------------------------------------------------ primitives

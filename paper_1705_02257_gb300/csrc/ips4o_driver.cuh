@@ -16,6 +16,7 @@
 
 #include "ips4o_host.h"
 #include "ips4o_kernels.cuh"
+#include "ips4o_segments.cuh"
 
 namespace ips4o {
 
@@ -34,7 +35,23 @@ struct Caps {
     u32 max_sub, max_stripes;
     u64 pool_cap, next_cap;
     u64 init_cap;       // segments that go straight to the base case (segmented calls)
+    u64 stack_cap;      // segment scheduler: buckets per CTA stack (0 = not used)
 };
+
+constexpr u64 kSegStackCap = 2048;     // per CTA; a distribution step pushes at most 256 buckets
+
+// Workspace of the segment scheduler (one slot per CTA of its persistent grid).
+template <class T>
+Caps<T> caps_for_scheduler(int sms, u64 num_segments) {
+    Caps<T> c;
+    c.max_sub = (u32)sms;
+    c.max_stripes = (u32)sms;
+    c.pool_cap = (u64)sms * kMaxBuckets * (T::kBlock - 1);
+    c.next_cap = 16;
+    c.init_cap = num_segments;
+    c.stack_cap = kSegStackCap;
+    return c;
+}
 
 // Base-case threshold in effect: buckets larger than this recurse.
 template <class T>
@@ -59,6 +76,7 @@ Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
     c.pool_cap = std::max<u64>(pool, (u64)kMaxBuckets * B);
     c.next_cap = n / (cap + 1) + 16;
     c.init_cap = 0;
+    c.stack_cap = 0;
     return c;
 }
 
@@ -100,12 +118,15 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.base_large = (Task*)take(S * kMaxBuckets * sizeof(Task));
     w.init_tasks = (Task*)take(c.init_cap * sizeof(Task));
     w.init_count = (u32*)take(2 * sizeof(u32));
+    w.hist = (u32*)take(65 * sizeof(u32));
+    w.stacks = (Task*)take(S * c.stack_cap * sizeof(Task));
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.max_sub = c.max_sub;
     w.max_stripes = c.max_stripes;
     w.pool_cap = c.pool_cap;
     w.next_cap = c.next_cap;
     w.init_cap = c.init_cap;
+    w.stack_cap = c.stack_cap;
     if (ws) *ws = w;
     return align_up(off, 256);
 }
@@ -151,6 +172,28 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
     } while (0)
 
 template <class T>
+ips4o_status set_kernel_attributes(DeviceState& st) {
+    IPS4O_CUDA(cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)ClassifyCfg<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)CleanupCfg<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseSmall<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)BaseSmall<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)BaseLarge<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_permute<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)PermuteCfg<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_segments<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)SegCfg<T>::smem_bytes));
+    int occ = 0;
+    IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB,
+                                                             PermuteCfg<T>::smem_bytes));
+    st.permute_grid[T::kId] = std::max(1, occ) * st.sms;
+    st.attrs_ready[T::kId] = true;
+    return IPS4O_OK;
+}
+
+template <class T>
 struct Driver {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
@@ -175,44 +218,52 @@ struct Driver {
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
     Driver(DeviceState& s, cudaStream_t strm, const ips4o_params& p) : st(s), stream(strm), prm(p) {}
 
-    ips4o_status setup(u64 n, u64 init_cap = 0) {
+    ips4o_status setup(u64 n, u64 init_cap = 0, const Caps<T>* override_caps = nullptr, bool may_allocate = true) {
         cudaGetLastError();   // an error left by an earlier, unrelated runtime call is not this call's
-        caps = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
-        caps.init_cap = init_cap;
+        st.d_status = nullptr;  // the workspace layout changes: an earlier status word is gone
+        if (override_caps) {
+            caps = *override_caps;
+        } else {
+            caps = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
+            caps.init_cap = init_cap;
+        }
         const size_t need = carve<T>(caps, nullptr, nullptr);
-        ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
+        ips4o_status rc = IPS4O_OK;
+        if (may_allocate) rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
+        else if (!st.d_ws || st.ws_bytes < need) rc = IPS4O_ERR_TOO_LARGE;
         if (rc != IPS4O_OK) return rc;
         carve<T>(caps, (char*)st.d_ws, &ws);
-        rc = ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(caps));
-        if (rc != IPS4O_OK) return rc;
-        char* h = (char*)st.h_stage;
-        h_subs = (SubDesc*)h;
-        h += align_up(caps.max_sub * sizeof(SubDesc), 256);
-        h_stripes = (StripeDesc*)h;
-        h += align_up(caps.max_stripes * sizeof(StripeDesc), 256);
-        h_ctr = (ChunkCounters*)h;
-        h += align_up(sizeof(ChunkCounters), 256);
-        h_tasks = (Task*)h;
+        if (may_allocate) {
+            rc = ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(caps));
+            if (rc != IPS4O_OK) return rc;
+            char* h = (char*)st.h_stage;
+            h_subs = (SubDesc*)h;
+            h += align_up(caps.max_sub * sizeof(SubDesc), 256);
+            h_stripes = (StripeDesc*)h;
+            h += align_up(caps.max_stripes * sizeof(StripeDesc), 256);
+            h_ctr = (ChunkCounters*)h;
+            h += align_up(sizeof(ChunkCounters), 256);
+            h_tasks = (Task*)h;
+        } else {
+            // enqueue-only calls never stage anything on the host
+            h_subs = nullptr;
+            h_stripes = nullptr;
+            h_ctr = nullptr;
+            h_tasks = nullptr;
+        }
         // a smaller base case than the capacity forces deeper recursion
         rec_cap = recursion_cap<T>(prm);
         base_cap = std::min((u32)T::kBaseSmall, rec_cap);
         k_max = (u32)std::min(256, std::max(4, prm.k_max));
         k_max = pow2_ceil_host(k_max);
         if (k_max > 256) k_max = 256;
-        IPS4O_CUDA(cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)ClassifyCfg<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)CleanupCfg<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseSmall<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)BaseSmall<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)BaseLarge<T>::smem_bytes));
-        IPS4O_CUDA(cudaFuncSetAttribute(k_permute<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)PermuteCfg<T>::smem_bytes));
-        int occ = 0;
-        IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB,
-                                                                 PermuteCfg<T>::smem_bytes));
-        permute_grid = std::max(1, occ) * st.sms;
+        // kernel attributes once per (stream state, element type): later calls,
+        // including ones made while a stream is captured, need no such calls
+        if (!st.attrs_ready[T::kId]) {
+            ips4o_status arc = set_kernel_attributes<T>(st);
+            if (arc != IPS4O_OK) return arc;
+        }
+        permute_grid = st.permute_grid[T::kId];
         st.stats = ips4o_stats{};
         st.stats.workspace_bytes = st.ws_bytes;
         return IPS4O_OK;
@@ -476,6 +527,64 @@ struct Driver {
         return levels(d, std::move(big), nullptr);
     }
 
+    // All segments by the persistent segment scheduler (one CTA per array,
+    // largest first).  The host only uploads the queue.
+    ips4o_status run_scheduler(E* d, const std::vector<Task>& segs) {
+        std::vector<Task> q;
+        q.reserve(segs.size());
+        u64 total = 0;
+        for (const Task& t : segs) {
+            total += t.n;
+            if (t.n >= 2) q.push_back(t);
+        }
+        std::sort(q.begin(), q.end(), [](const Task& a, const Task& b) { return a.n > b.n; });
+        const Caps<T> c = caps_for_scheduler<T>(st.sms, q.size());
+        ips4o_status rc = setup(total, 0, &c);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = total;
+        if (q.empty()) return IPS4O_OK;
+        const u32 cnt[2] = {(u32)q.size(), 0u};
+        IPS4O_CUDA(cudaMemcpyAsync(ws.init_tasks, q.data(), q.size() * sizeof(Task), cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemcpyAsync(ws.init_count, cnt, sizeof cnt, cudaMemcpyHostToDevice, stream));
+        IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
+        const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
+        IPS4O_LAUNCH(4, (k_segments<T><<<st.sms, SegCfg<T>::TPB, SegCfg<T>::smem_bytes, stream>>>(
+                            d, ws, sq, prm.seed, k_max, kSpinLimit)));
+        IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
+        IPS4O_CUDA(cudaStreamSynchronize(stream));
+        IPS4O_CUDA(cudaGetLastError());
+        rc = collect_events();
+        if (rc != IPS4O_OK) return rc;
+        st.stats.blocks_moved += h_ctr->blocks_moved;
+        st.stats.blocks_skipped += h_ctr->blocks_skipped;
+        st.stats.base_case_buckets += h_ctr->base_buckets;
+        st.stats.subproblems = h_ctr->next_count;      // distribution steps run by the CTAs
+        st.stats.levels = h_ctr->next_count ? 1 : 0;  // at least one level (depth is not tracked)
+        st.stats.chunks = 1;
+        return status_from(h_ctr->status);
+    }
+
+    // The same with the offsets in device memory and nothing but enqueued
+    // work: no allocation, no host synchronisation (capturable in a CUDA
+    // graph).  The workspace must have been reserved.  Errors land in the
+    // status word that ips4o_stream_status reads.
+    ips4o_status enqueue_scheduler(E* d, const u64* d_off, u64 num_segments) {
+        const Caps<T> c = caps_for_scheduler<T>(st.sms, num_segments);
+        ips4o_status rc = setup(0, 0, &c, false);
+        if (rc != IPS4O_OK) return rc;
+        st.d_status = &ws.ctr->status;
+        IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
+        IPS4O_CUDA(cudaMemsetAsync(ws.hist, 0, 65 * sizeof(u32), stream));
+        const int g = (int)std::min<u64>((num_segments + 255) / 256, (u64)st.sms * 4);
+        IPS4O_LAUNCH(7, (k_seg_hist<<<g, 256, 0, stream>>>(d_off, num_segments, ws.hist)));
+        IPS4O_LAUNCH(7, (k_seg_scan<<<1, 32, 0, stream>>>(ws.hist, ws.init_count, ws.init_count + 1)));
+        IPS4O_LAUNCH(7, (k_seg_fill<<<g, 256, 0, stream>>>(d_off, num_segments, ws.hist, ws.init_tasks, ws.ctr)));
+        const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
+        IPS4O_LAUNCH(4, (k_segments<T><<<st.sms, SegCfg<T>::TPB, SegCfg<T>::smem_bytes, stream>>>(
+                            d, ws, sq, prm.seed, k_max, kSpinLimit)));
+        return IPS4O_OK;
+    }
+
     ips4o_status levels(E* d, std::vector<Task> level_tasks, PartitionOut* part) {
         ips4o_status rc = IPS4O_OK;
         std::vector<Task> next;
@@ -543,15 +652,30 @@ ips4o_status reserve_t(DeviceState& st, u64 n, u64 num_segments) {
     const ips4o_params& prm = global_params();
     Caps<T> c = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
     c.init_cap = num_segments;
-    ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, carve<T>(c, nullptr, nullptr));
+    const size_t need = std::max(carve<T>(c, nullptr, nullptr),
+                                 carve<T>(caps_for_scheduler<T>(st.sms, num_segments), nullptr, nullptr));
+    ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
     if (rc != IPS4O_OK) return rc;
+    if (!st.attrs_ready[T::kId] && (rc = set_kernel_attributes<T>(st)) != IPS4O_OK) return rc;
     return ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(c));
 }
 
+// Segmented calls that may synchronise take the level-by-level path unless
+// the segment scheduler is asked for: measured on GB300 with 2^28 u64 keys
+// in arrays of log-uniform lengths up to 2^20, level by level sorts about
+// 30 G keys/s and the scheduler about 25 G keys/s.  The enqueue-only entry
+// point always uses the scheduler.
 template <class T>
 ips4o_status sort_segments_t(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s) {
     Driver<T> drv(st, s);
+    if (global_params().segment_scheduler == 2) return drv.run_scheduler((typename T::elem_t*)d, segs);
     return drv.run_segments((typename T::elem_t*)d, segs);
+}
+
+template <class T>
+ips4o_status enqueue_segments_t(DeviceState& st, void* d, const u64* d_off, u64 num_segments, cudaStream_t s) {
+    Driver<T> drv(st, s);
+    return drv.enqueue_scheduler((typename T::elem_t*)d, d_off, num_segments);
 }
 
 }  // namespace ips4o

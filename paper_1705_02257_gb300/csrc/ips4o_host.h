@@ -22,6 +22,9 @@ struct DeviceState {
     size_t d_host_copy_bytes = 0;
     void* d_aux = nullptr;          // 100-byte records: pairs, input copy, run bounds
     size_t aux_bytes = 0;
+    unsigned* d_status = nullptr;   // status word of the last enqueue-only call on this stream
+    bool attrs_ready[4] = {false, false, false, false};   // kernel attributes set, per element type
+    int permute_grid[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> events;
     std::mutex mtx;
     ips4o_stats stats{};
@@ -49,6 +52,9 @@ ips4o_status sort_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Partit
 ips4o_status sort_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
 struct Task;
 ips4o_status sort_segments_u64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+ips4o_status enqueue_segments_u64(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s);
+ips4o_status enqueue_segments_f64(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s);
+ips4o_status enqueue_segments_pair(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s);
 ips4o_status sort_segments_f64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
 ips4o_status sort_segments_pair(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
 // ips4o_sort_noalloc's level loop; tasks = 2 * kNoAllocMaxTasks entries

@@ -35,14 +35,12 @@
 namespace ips4o {
 
 // ------------------------------------------------------------- sampling
+// Sample and splitters of subproblem j by the whole CTA (TPB threads, at
+// least 256): keys[4096], cand[256] and scan_tmp[32] are shared memory.
 template <class T, int TPB>
-__global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u64 seed) {
+__device__ void sample_sub(const typename T::elem_t* arr, const Workspace<T>& ws, u32 j, u64 seed,
+                           typename T::key_t* keys, typename T::key_t* cand, u32* scan_tmp) {
     typedef typename T::key_t K;
-    __shared__ K keys[4096];
-    __shared__ K cand[256];
-    __shared__ u32 scan_tmp[32];
-    const u32 j = blockIdx.x;
-    if (j >= nsub) return;
     SubDesc d = ws.subs[j];
     const u32 kk = d.k_target;                 // power of two in [2, 256]
     const u32 alpha = d.alpha;
@@ -70,6 +68,18 @@ __global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, W
         ws.subs[j].eq = eq ? 1u : 0u;
         ws.subs[j].nbuckets = eq ? 2 * L - 1 : L;
     }
+    __syncthreads();
+}
+
+template <class T, int TPB>
+__global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u64 seed) {
+    typedef typename T::key_t K;
+    __shared__ K keys[4096];
+    __shared__ K cand[256];
+    __shared__ u32 scan_tmp[32];
+    const u32 j = blockIdx.x;
+    if (j >= nsub) return;
+    sample_sub<T, TPB>(arr, ws, j, seed, keys, cand, scan_tmp);
 }
 
 // ------------------------------------------------- local classification
@@ -172,14 +182,14 @@ __device__ __forceinline__ void classify_many(const u64 (&k)[IPT], const u32* th
     }
 }
 
+// Local classification of stripe s (Section 4.1) by the whole CTA
+// (ClassifyCfg<T>::TPB threads, ClassifyCfg<T>::smem_bytes of shared memory).
 template <class T>
-__global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
-    k_classify(typename T::elem_t* arr, Workspace<T> ws, u32 nstripes) {
+__device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws, u32 s, unsigned char* smem_raw) {
     typedef ClassifyCfg<T> C;
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     constexpr int TPB = C::TPB, NW = C::NW, STAGES = C::STAGES, TILE = C::TILE, IPT = C::IPT, B = C::B;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     E* buf = (E*)(smem_raw + C::off_buf);
     E* stage = (E*)(smem_raw + C::off_stage);
     K* s_tree = (K*)(smem_raw + C::off_tree);
@@ -191,14 +201,9 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
     u32* s_total = (u32*)(smem_raw + C::off_total);
     unsigned short* s_blkb = (unsigned short*)(smem_raw + C::off_blkb);
     unsigned short* s_emit = (unsigned short*)(smem_raw + C::off_emit);   // buckets emitting in this tile
-    u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp, [40] stripe id
+    u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    for (;;) {
-        if (tid == 0) s_misc[40] = atomicAdd(&ws.ctr->stripe_next, 1u);
-        __syncthreads();
-        const u32 s = (u32)s_misc[40];
-        if (s >= nstripes) break;
+    {
         const StripeDesc sd = ws.stripes[s];
         const SubDesc sub = ws.subs[sd.sub];
         const int logL = (int)sub.log_leaves;
@@ -361,17 +366,30 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
     }
 }
 
+template <class T>
+__global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
+    k_classify(typename T::elem_t* arr, Workspace<T> ws, u32 nstripes) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ u32 s_stripe;
+    for (;;) {
+        if (threadIdx.x == 0) s_stripe = atomicAdd(&ws.ctr->stripe_next, 1u);
+        __syncthreads();
+        const u32 s = s_stripe;
+        __syncthreads();
+        if (s >= nstripes) break;
+        classify_stripe<T>(arr, ws, s, smem_raw);
+    }
+}
+
 // ----------------------------------------------- prefix sums, pointers
+// Bucket starts, delimiters, (w, r) words, empty-block fix list and the
+// exhausted bitmap of subproblem j, by a CTA of TPB >= 256 threads (thread b
+// handles bucket b).  Shared memory: tmp64[32], s_sbk and s_full
+// [kMaxStripesPerSub], s_delim[kMaxBuckets + 1].
 template <class T, int TPB>
-__global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
+__device__ void prefix_sub(const Workspace<T>& ws, u32 j, u64* tmp64, u32* s_sbk, u32* s_full, u32* s_delim) {
     constexpr int B = T::kBlock;
-    static_assert(TPB == kMaxBuckets, "one thread per bucket");
-    __shared__ u64 tmp64[32];
-    __shared__ u32 s_sbk[kMaxStripesPerSub];
-    __shared__ u32 s_full[kMaxStripesPerSub];
-    __shared__ u32 s_delim[kMaxBuckets + 1];
-    const u32 j = blockIdx.x;
-    if (j >= nsub) return;
+    static_assert(TPB >= kMaxBuckets && TPB % 32 == 0, "one thread per bucket");
     const SubDesc sub = ws.subs[j];
     const u32 nb = sub.nbuckets;
     const u32 sb = sub.stripe_begin, ns = sub.num_stripes;
@@ -446,11 +464,23 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
     // buckets without unprocessed blocks (beyond nb, no full block in the
     // region, or all in place) start out exhausted: no mover probes them
     const u32 word = __ballot_sync(0xffffffffu, no_blocks);
-    if ((b & 31) == 0) ws.exhausted[(u64)j * 8 + (b >> 5)] = word;
+    if ((b & 31) == 0 && b < kMaxBuckets) ws.exhausted[(u64)j * 8 + (b >> 5)] = word;
     if (threadIdx.x == 0) {
         for (u32 i = 0; i < ns; ++i) blocks += s_full[i];
         ws.subs[j].blocks_total = blocks;
     }
+    __syncthreads();
+}
+
+template <class T, int TPB>
+__global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
+    __shared__ u64 tmp64[32];
+    __shared__ u32 s_sbk[kMaxStripesPerSub];
+    __shared__ u32 s_full[kMaxStripesPerSub];
+    __shared__ u32 s_delim[kMaxBuckets + 1];
+    const u32 j = blockIdx.x;
+    if (j >= nsub) return;
+    prefix_sub<T, TPB>(ws, j, tmp64, s_sbk, s_full, s_delim);
 }
 
 // -------------------------------------------- empty-block movement (App. A)
@@ -574,6 +604,179 @@ struct PermuteCfg {
     static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
 };
 
+// One mover group (a warp of V movers) of subproblem j: group gl of the
+// subproblem's groups, nmov movers in all (Section 4.2).  wbuf is the warp's
+// [2][V][b] block buffer; tree, spl, delim its copies of the subproblem's
+// search tree, splitters and delimiters (shared memory).
+template <class T>
+__device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Workspace<T>& ws, u32 j, u32 gl,
+                                              u32 nmov, typename T::elem_t* wbuf, typename T::key_t* tree,
+                                              typename T::key_t* spl, u32* delim, u32 spin_limit, u64& moved,
+                                              u64& skipped, bool& failed) {
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
+    typedef PermuteCfg<T> C;
+    constexpr int V = C::V, EPL = C::EPL, B = T::kBlock;
+    const int lane = threadIdx.x & 31;
+    const bool is_mover = lane < V;
+    const SubDesc sub = ws.subs[j];
+    const u32 nb = sub.nbuckets;
+    const int logL = (int)sub.log_leaves;
+    const bool eq = sub.eq != 0;
+    // this warp's copy of the subproblem's tree, splitters and delimiters
+    __syncwarp();
+    for (int i = lane; i < kMaxLeaves; i += 32) {
+        tree[i] = ws.tree[(u64)j * kMaxLeaves + i];
+        spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
+    }
+    for (int i = lane; i <= kMaxBuckets; i += 32) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
+    __syncwarp();
+    u64* wr = ws.wr + (u64)j * kMaxBuckets;
+    u32* exh = ws.exhausted + (u64)j * 8;
+    E* A = arr + sub.begin;
+    E* ovf = ws.overflow + (u64)j * B;
+    const u64 nbc = sub.n / B;                   // complete block slots
+    const bool partial = (sub.n % B) != 0;
+
+    // per-lane mover state (lanes >= V never become active)
+    u32 prim = is_mover ? (u32)(((u64)(gl * V + lane) * nb) / nmov) : 0u;
+    u32 tgt = 0, hand = 0;                     // hand: which of the two buffers holds the carried block
+    bool have = false, done = !is_mover;
+    u32 exw[8];
+#pragma unroll
+    for (int w8 = 0; w8 < 8; ++w8) exw[w8] = 0;
+    bool exw_valid = false;
+    for (;;) {
+        if (!__any_sync(0xffffffffu, !done) || failed) break;
+        // ---- one claim per active mover
+        u64 old = 0;
+        if (!done) {
+            if (have) old = atom_add_acquire(&wr[tgt], kClaimWrite);
+            else old = atomicAdd(&wr[prim], kClaimRead);
+        }
+        const long long w = pk_w(old), r = pk_r(old);
+        const u32 rd = pk_readers(old);
+        bool ldn = false, ldt = false, emp = false, exd = false;
+        u64 slot = 0;
+        if (!done) {
+            if (!have) {
+                if (r < w) {
+                    // no unprocessed block left in the primary bucket: undo
+                    red_add_relaxed64(&wr[prim], kReadDone);
+                    atomicOr(&exh[prim >> 5], 1u << (prim & 31));
+                    exd = true;
+                } else {
+                    slot = (u64)delim[prim] + (u64)r;
+                    if (IPS4O_GUARD(ws.ctr, r >= 0 && slot < nbc, slot, nbc)) ldn = true;
+                    else failed = true;
+                }
+            } else {
+                slot = (u64)delim[tgt] + (u64)w;
+                if (!IPS4O_GUARD(ws.ctr, slot < delim[tgt + 1], slot, delim[tgt + 1])) {
+                    failed = true;
+                } else if (w <= r) {
+                    if (IPS4O_GUARD(ws.ctr, slot < nbc, slot, nbc)) ldt = true;
+                    else failed = true;
+                } else {
+                    emp = true;
+                }
+            }
+        }
+        if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
+        // ---- block loads of all movers, one coalesced copy per block
+        {
+            unsigned m = __ballot_sync(0xffffffffu, ldn || ldt);
+            while (m) {
+                const int v = __ffs(m) - 1;
+                m &= m - 1;
+                const u64 sv = __shfl_sync(0xffffffffu, slot, v);
+                const u32 hb = __shfl_sync(0xffffffffu, hand, v) ^ 1u;      // the free buffer
+                E* dst = wbuf + ((size_t)hb * V + v) * B;
+                const E* src = A + sv * B;
+#pragma unroll
+                for (int q = 0; q < EPL; ++q) cp_async<sizeof(E)>(dst + lane + 32 * q, src + lane + 32 * q);
+            }
+            cp_async_commit();
+            cp_async_wait<0>();
+            __syncwarp();
+        }
+        // The warp barrier orders every lane's copies of the claimed blocks
+        // before the release that drops the reader count (release is
+        // cumulative): a writer that sees the count drained cannot overwrite
+        // a slot that is still being read.  Counts are dropped before this
+        // warp waits on any count, so movers of one warp never wait on each
+        // other.
+        if (ldn) red_add_release64(&wr[prim], kReadDone);
+        // ---- writes into empty slots (after the reader counts drained)
+        bool ok = true;
+        if (emp && rd != 0) {
+            u32 it = 0;
+            while (pk_readers(ld_acquire64(&wr[tgt])) != 0) {
+                if (++it > spin_limit) { ok = false; break; }
+                __nanosleep(32);
+            }
+        }
+        if (!ok) set_status(ws.ctr, kStatusTimeout);
+        if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
+        bool bad_slot = emp && !(slot < nbc || (partial && slot == nbc));
+        if (bad_slot) IPS4O_GUARD(ws.ctr, false, slot, nbc);
+        if (__any_sync(0xffffffffu, bad_slot)) { failed = true; break; }
+        // ---- classify the head of every block just loaded
+        int t = 0;
+        if (ldn || ldt) {
+            const E* blk = wbuf + ((size_t)(hand ^ 1u) * V + lane) * B;
+            t = classify_key<K>(T::key(blk[0]), tree, spl, logL, eq);
+            if (!IPS4O_GUARD(ws.ctr, t >= 0 && (u32)t < nb, t, nb)) failed = true;
+        }
+        if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
+        const bool swp = ldt && (u32)t != tgt;           // the slot's block must move on
+        if (ldt && !swp) ++skipped;                       // already in its bucket: leave it
+        // ---- stores: carried blocks into empty slots and swap slots
+        {
+            unsigned m = __ballot_sync(0xffffffffu, emp || swp);
+            while (m) {
+                const int v = __ffs(m) - 1;
+                m &= m - 1;
+                const u64 sv = __shfl_sync(0xffffffffu, slot, v);
+                const u32 hb = __shfl_sync(0xffffffffu, hand, v);
+                const E* src = wbuf + ((size_t)hb * V + v) * B;
+                E* dst = sv < nbc ? A + sv * B : ovf;
+#pragma unroll
+                for (int q = 0; q < EPL; ++q) dst[lane + 32 * q] = src[lane + 32 * q];
+            }
+            __syncwarp();
+        }
+        if (emp) { have = false; ++moved; }
+        if (swp) { hand ^= 1u; tgt = (u32)t; ++moved; }
+        if (ldn) { hand ^= 1u; tgt = (u32)t; have = true; }
+        // ---- movers whose primary bucket ran dry pick the next live one
+        if (__any_sync(0xffffffffu, exd)) {
+            if (exd) {
+#pragma unroll
+                for (int w8 = 0; w8 < 8; ++w8) exw[w8] = ld_relaxed(&exh[w8]);
+                exw_valid = true;
+                // first non-exhausted bucket after prim, cyclically
+                u32 np = 0xffffffffu;
+                for (u32 step = 1; step <= 8 * 32 && np == 0xffffffffu; ) {
+                    const u32 c = (prim + step) & 255u;
+                    const u32 free_bits = ~exw[c >> 5] >> (c & 31);
+                    if (free_bits) {
+                        const u32 cand = c + (u32)(__ffs(free_bits) - 1);
+                        // a candidate past the end of this word wraps at bit 31
+                        np = cand;
+                    } else {
+                        step += 32 - (c & 31);
+                    }
+                }
+                if (np == 0xffffffffu) done = true;
+                else if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim = np;
+                else { failed = true; done = true; }
+            }
+        }
+        (void)exw_valid;
+    }
+}
+
 template <class T>
 __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
     k_permute(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit) {
@@ -642,162 +845,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
         const u32 j = lo;
         const u32 gl = g - s_gpre[j];
         const u32 nmov = (s_gpre[j + 1] - s_gpre[j]) * V;
-        const SubDesc sub = ws.subs[j];
-        const u32 nb = sub.nbuckets;
-        const int logL = (int)sub.log_leaves;
-        const bool eq = sub.eq != 0;
-        // this warp's copy of the subproblem's tree, splitters and delimiters
-        __syncwarp();
-        for (int i = lane; i < kMaxLeaves; i += 32) {
-            tree[i] = ws.tree[(u64)j * kMaxLeaves + i];
-            spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
-        }
-        for (int i = lane; i <= kMaxBuckets; i += 32) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
-        __syncwarp();
-        u64* wr = ws.wr + (u64)j * kMaxBuckets;
-        u32* exh = ws.exhausted + (u64)j * 8;
-        E* A = arr + sub.begin;
-        E* ovf = ws.overflow + (u64)j * B;
-        const u64 nbc = sub.n / B;                   // complete block slots
-        const bool partial = (sub.n % B) != 0;
-
-        // per-lane mover state (lanes >= V never become active)
-        u32 prim = is_mover ? (u32)(((u64)(gl * V + lane) * nb) / nmov) : 0u;
-        u32 tgt = 0, hand = 0;                     // hand: which of the two buffers holds the carried block
-        bool have = false, done = !is_mover;
-        u32 exw[8];
-#pragma unroll
-        for (int w8 = 0; w8 < 8; ++w8) exw[w8] = 0;
-        bool exw_valid = false;
-        for (;;) {
-            if (!__any_sync(0xffffffffu, !done) || failed) break;
-            // ---- one claim per active mover
-            u64 old = 0;
-            if (!done) {
-                if (have) old = atom_add_acquire(&wr[tgt], kClaimWrite);
-                else old = atomicAdd(&wr[prim], kClaimRead);
-            }
-            const long long w = pk_w(old), r = pk_r(old);
-            const u32 rd = pk_readers(old);
-            bool ldn = false, ldt = false, emp = false, exd = false;
-            u64 slot = 0;
-            if (!done) {
-                if (!have) {
-                    if (r < w) {
-                        // no unprocessed block left in the primary bucket: undo
-                        red_add_relaxed64(&wr[prim], kReadDone);
-                        atomicOr(&exh[prim >> 5], 1u << (prim & 31));
-                        exd = true;
-                    } else {
-                        slot = (u64)delim[prim] + (u64)r;
-                        if (IPS4O_GUARD(ws.ctr, r >= 0 && slot < nbc, slot, nbc)) ldn = true;
-                        else failed = true;
-                    }
-                } else {
-                    slot = (u64)delim[tgt] + (u64)w;
-                    if (!IPS4O_GUARD(ws.ctr, slot < delim[tgt + 1], slot, delim[tgt + 1])) {
-                        failed = true;
-                    } else if (w <= r) {
-                        if (IPS4O_GUARD(ws.ctr, slot < nbc, slot, nbc)) ldt = true;
-                        else failed = true;
-                    } else {
-                        emp = true;
-                    }
-                }
-            }
-            if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
-            // ---- block loads of all movers, one coalesced copy per block
-            {
-                unsigned m = __ballot_sync(0xffffffffu, ldn || ldt);
-                while (m) {
-                    const int v = __ffs(m) - 1;
-                    m &= m - 1;
-                    const u64 sv = __shfl_sync(0xffffffffu, slot, v);
-                    const u32 hb = __shfl_sync(0xffffffffu, hand, v) ^ 1u;      // the free buffer
-                    E* dst = wbuf + ((size_t)hb * V + v) * B;
-                    const E* src = A + sv * B;
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) cp_async<sizeof(E)>(dst + lane + 32 * q, src + lane + 32 * q);
-                }
-                cp_async_commit();
-                cp_async_wait<0>();
-                __syncwarp();
-            }
-            // The warp barrier orders every lane's copies of the claimed blocks
-            // before the release that drops the reader count (release is
-            // cumulative): a writer that sees the count drained cannot overwrite
-            // a slot that is still being read.  Counts are dropped before this
-            // warp waits on any count, so movers of one warp never wait on each
-            // other.
-            if (ldn) red_add_release64(&wr[prim], kReadDone);
-            // ---- writes into empty slots (after the reader counts drained)
-            bool ok = true;
-            if (emp && rd != 0) {
-                u32 it = 0;
-                while (pk_readers(ld_acquire64(&wr[tgt])) != 0) {
-                    if (++it > spin_limit) { ok = false; break; }
-                    __nanosleep(32);
-                }
-            }
-            if (!ok) set_status(ws.ctr, kStatusTimeout);
-            if (__any_sync(0xffffffffu, !ok)) { failed = true; break; }
-            bool bad_slot = emp && !(slot < nbc || (partial && slot == nbc));
-            if (bad_slot) IPS4O_GUARD(ws.ctr, false, slot, nbc);
-            if (__any_sync(0xffffffffu, bad_slot)) { failed = true; break; }
-            // ---- classify the head of every block just loaded
-            int t = 0;
-            if (ldn || ldt) {
-                const E* blk = wbuf + ((size_t)(hand ^ 1u) * V + lane) * B;
-                t = classify_key<K>(T::key(blk[0]), tree, spl, logL, eq);
-                if (!IPS4O_GUARD(ws.ctr, t >= 0 && (u32)t < nb, t, nb)) failed = true;
-            }
-            if (__any_sync(0xffffffffu, failed)) { failed = true; break; }
-            const bool swp = ldt && (u32)t != tgt;           // the slot's block must move on
-            if (ldt && !swp) ++skipped;                       // already in its bucket: leave it
-            // ---- stores: carried blocks into empty slots and swap slots
-            {
-                unsigned m = __ballot_sync(0xffffffffu, emp || swp);
-                while (m) {
-                    const int v = __ffs(m) - 1;
-                    m &= m - 1;
-                    const u64 sv = __shfl_sync(0xffffffffu, slot, v);
-                    const u32 hb = __shfl_sync(0xffffffffu, hand, v);
-                    const E* src = wbuf + ((size_t)hb * V + v) * B;
-                    E* dst = sv < nbc ? A + sv * B : ovf;
-#pragma unroll
-                    for (int q = 0; q < EPL; ++q) dst[lane + 32 * q] = src[lane + 32 * q];
-                }
-                __syncwarp();
-            }
-            if (emp) { have = false; ++moved; }
-            if (swp) { hand ^= 1u; tgt = (u32)t; ++moved; }
-            if (ldn) { hand ^= 1u; tgt = (u32)t; have = true; }
-            // ---- movers whose primary bucket ran dry pick the next live one
-            if (__any_sync(0xffffffffu, exd)) {
-                if (exd) {
-#pragma unroll
-                    for (int w8 = 0; w8 < 8; ++w8) exw[w8] = ld_relaxed(&exh[w8]);
-                    exw_valid = true;
-                    // first non-exhausted bucket after prim, cyclically
-                    u32 np = 0xffffffffu;
-                    for (u32 step = 1; step <= 8 * 32 && np == 0xffffffffu; ) {
-                        const u32 c = (prim + step) & 255u;
-                        const u32 free_bits = ~exw[c >> 5] >> (c & 31);
-                        if (free_bits) {
-                            const u32 cand = c + (u32)(__ffs(free_bits) - 1);
-                            // a candidate past the end of this word wraps at bit 31
-                            np = cand;
-                        } else {
-                            step += 32 - (c & 31);
-                        }
-                    }
-                    if (np == 0xffffffffu) done = true;
-                    else if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim = np;
-                    else { failed = true; done = true; }
-                }
-            }
-            (void)exw_valid;
-        }
+        permute_group<T>(arr, ws, j, gl, nmov, wbuf, tree, spl, delim, spin_limit, moved, skipped, failed);
     }
     if (moved) atomicAdd(&ws.ctr->blocks_moved, moved);
     if (skipped) atomicAdd(&ws.ctr->blocks_skipped, skipped);

@@ -44,7 +44,8 @@ class Ips4oError(RuntimeError):
 
 class Params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("alpha", ctypes.c_int), ("base_case_max", ctypes.c_int),
-                ("stripes_per_sm", ctypes.c_int), ("profile", ctypes.c_int), ("seed", ctypes.c_uint64)]
+                ("stripes_per_sm", ctypes.c_int), ("profile", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("segment_scheduler", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -75,6 +76,8 @@ def _load():
     lib.ips4o_sort_noalloc.argtypes = [vp, sz, i32, vp]
     lib.ips4o_sort_segmented.restype = i32
     lib.ips4o_sort_segmented.argtypes = [vp, vp, sz, i32, vp]
+    lib.ips4o_sort_segmented_async.restype = i32
+    lib.ips4o_sort_segmented_async.argtypes = [vp, vp, sz, i32, vp]
     lib.ips4o_sort_batched.restype = i32
     lib.ips4o_sort_batched.argtypes = [vp, vp, sz, i32, vp]
     lib.ips4o_stream_status.restype = i32
@@ -127,6 +130,11 @@ def ips4o_sort_noalloc(d_ptr: int, n: int, key_type: int, stream: int = 0) -> in
 def ips4o_sort_segmented(d_base: int, offsets: int, num_segments: int, key_type: int, stream: int = 0) -> int:
     """offsets: address of num_segments + 1 uint64 element indices (host or device)."""
     return _lib.ips4o_sort_segmented(d_base, offsets, num_segments, key_type, stream)
+
+
+def ips4o_sort_segmented_async(d_base: int, d_offsets: int, num_segments: int, key_type: int, stream: int = 0) -> int:
+    """Enqueue-only segmented sort (device offsets; reserve the workspace first)."""
+    return _lib.ips4o_sort_segmented_async(d_base, d_offsets, num_segments, key_type, stream)
 
 
 def ips4o_sort_batched(ptrs: int, lens: int, count: int, key_type: int, stream: int = 0) -> int:

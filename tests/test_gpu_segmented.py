@@ -28,6 +28,15 @@ def ips4o():
     return m
 
 
+@pytest.fixture(params=[1, 2], ids=["levels", "scheduler"])
+def mode(request, ips4o):
+    """Both processing forms of segmented and batched calls: level by level
+    across all segments (1) and the segment scheduler, one CTA per array (2)."""
+    ips4o.set_params(segment_scheduler=request.param)
+    yield request.param
+    ips4o.reset_params()
+
+
 def to_dev(a):
     return torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1).copy()).cuda()
 
@@ -55,7 +64,7 @@ def check_segments(got, a, off, kt):
 
 @pytest.mark.parametrize("kt,dist", [("u64", "uniform"), ("u64", "two_dup"), ("f64", "uniform"),
                                      ("pair", "root_dup"), ("u64", "ones")])
-def test_segmented_log_uniform_lengths(ips4o, kt, dist):
+def test_segmented_log_uniform_lengths(ips4o, mode, kt, dist):
     lengths = inputs.log_uniform_lengths(1000, 4, 17)
     off = offsets_for(lengths)
     a = inputs.make(kt, int(off[-1]), dist)
@@ -64,7 +73,7 @@ def test_segmented_log_uniform_lengths(ips4o, kt, dist):
     check_segments(to_host(t, a), a, off, kt)
 
 
-def test_segmented_offsets_on_device_and_untouched_margins(ips4o):
+def test_segmented_offsets_on_device_and_untouched_margins(ips4o, mode):
     lengths = np.array([0, 1, 2, 3, 17, 0, 8192, 8193, 16384, 16385, 70_000, 1, 200_003], dtype=np.uint64)
     start = 1000
     off = offsets_for(lengths, start)
@@ -79,7 +88,7 @@ def test_segmented_offsets_on_device_and_untouched_margins(ips4o):
     check_segments(got, a, off, "u64")
 
 
-def test_segmented_equals_each_segment_sorted_alone(ips4o):
+def test_segmented_equals_each_segment_sorted_alone(ips4o, mode):
     lengths = inputs.log_uniform_lengths(300, 4, 19)
     off = offsets_for(lengths)
     a = inputs.pair(int(off[-1]), "eight_dup")
@@ -96,7 +105,7 @@ def test_segmented_equals_each_segment_sorted_alone(ips4o):
                               np.sort(alone, order=["key", "payload"]))
 
 
-def test_segmented_all_large_segments(ips4o):
+def test_segmented_all_large_segments(ips4o, mode):
     lengths = np.array([300_001, 1 << 20, 65_536, 2_000_000, 500_000], dtype=np.uint64)
     off = offsets_for(lengths)
     a = inputs.u64(int(off[-1]), "exponential")
@@ -110,7 +119,7 @@ def test_segmented_all_large_segments(ips4o):
 
 @pytest.mark.parametrize("k_max,bcm", [(16, 64), (256, 100)])
 def test_segmented_deep_recursion(ips4o, k_max, bcm):
-    ips4o.set_params(k_max=k_max, base_case_max=bcm)
+    ips4o.set_params(k_max=k_max, base_case_max=bcm, segment_scheduler=1)
     try:
         lengths = inputs.log_uniform_lengths(200, 4, 16)
         off = offsets_for(lengths)
@@ -122,7 +131,7 @@ def test_segmented_deep_recursion(ips4o, k_max, bcm):
         ips4o.reset_params()
 
 
-def test_batched_separate_arrays_with_gaps(ips4o):
+def test_batched_separate_arrays_with_gaps(ips4o, mode):
     """Arrays carved out of one allocation with gaps between them, passed
     in a shuffled order: the gaps keep their bytes."""
     lengths = inputs.log_uniform_lengths(120, 4, 18)
@@ -143,7 +152,7 @@ def test_batched_separate_arrays_with_gaps(ips4o):
     assert np.array_equal(got[mask], a[mask])
 
 
-def test_batched_device_tables_and_empty_arrays(ips4o):
+def test_batched_device_tables_and_empty_arrays(ips4o, mode):
     arrs = [to_dev(inputs.f64(L, seed=10 + i)) for i, L in enumerate([0, 5, 100_000, 0, 20_000])]
     ptrs = torch.tensor([x.data_ptr() for x in arrs], dtype=torch.int64).cuda()
     lens = torch.tensor([x.numel() // 8 for x in arrs], dtype=torch.int64).cuda()
@@ -197,3 +206,77 @@ def test_streams_run_side_by_side(ips4o):
     assert not errors, errors
     for a, t in zip(arrays, tens):
         assert np.array_equal(to_host(t, a), oracle.sort(a, "u64"))
+
+
+def test_scheduler_heavy_duplicates_and_deep_segments(ips4o):
+    """The segment scheduler on arrays whose buckets need further
+    distribution steps by the same CTA (Exponential keys leave some buckets
+    above the base case) and on arrays of one repeated key."""
+    ips4o.set_params(segment_scheduler=2)
+    try:
+        lengths = np.array([4_000_000, 1 << 20, 300_000, 70_001, 16_385, 9, 2_000_000], dtype=np.uint64)
+        off = offsets_for(lengths)
+        for dist in ("exponential", "ones", "two_dup", "root_dup"):
+            a = inputs.u64_segments(lengths, dist)
+            t = to_dev(a)
+            ips4o.sort_segmented(t, off, "u64")
+            check_segments(to_host(t, a), a, off, "u64")
+    finally:
+        ips4o.reset_params()
+
+
+def _async_sort(ips4o, t, d_off, nseg, kt, stream):
+    rc = ips4o.ips4o_sort_segmented_async(t.data_ptr(), d_off.data_ptr(), nseg, ips4o.KEY_TYPES[kt],
+                                          stream.cuda_stream)
+    assert rc == 0, ips4o.STATUS.get(rc)
+
+
+@pytest.mark.parametrize("kt,dist", [("u64", "uniform"), ("pair", "two_dup"), ("f64", "exponential")])
+def test_segmented_async_and_stream_status(ips4o, kt, dist):
+    lengths = inputs.log_uniform_lengths(700, 4, 18)
+    off = offsets_for(lengths)
+    a = inputs.make(kt, int(off[-1]), dist)
+    t = to_dev(a)
+    d_off = torch.from_numpy(off.view(np.int64).copy()).cuda()
+    stream = torch.cuda.Stream()
+    # nothing reserved on this stream yet: refused before any work
+    assert ips4o.ips4o_sort_segmented_async(t.data_ptr(), d_off.data_ptr(), len(lengths),
+                                            ips4o.KEY_TYPES[kt], stream.cuda_stream) == 8
+    assert ips4o.ips4o_reserve_workspace(int(off[-1]), len(lengths), ips4o.KEY_TYPES[kt], stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    _async_sort(ips4o, t, d_off, len(lengths), kt, stream)
+    assert ips4o.ips4o_stream_status(stream.cuda_stream) == 0
+    check_segments(to_host(t, a), a, off, kt)
+
+
+def test_segmented_async_reports_decreasing_offsets(ips4o):
+    t = torch.zeros(1000, dtype=torch.int64).cuda()
+    off = torch.tensor([0, 500, 400, 1000], dtype=torch.int64).cuda()
+    stream = torch.cuda.Stream()
+    assert ips4o.ips4o_reserve_workspace(1000, 3, ips4o.U64, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    assert ips4o.ips4o_sort_segmented_async(t.data_ptr(), off.data_ptr(), 3, ips4o.U64, stream.cuda_stream) == 0
+    assert ips4o.ips4o_stream_status(stream.cuda_stream) == 7
+
+
+def test_segmented_async_in_a_cuda_graph(ips4o):
+    """Captured once into a CUDA graph, replayed on new contents of the same
+    buffers: every replay sorts every array."""
+    lengths = inputs.log_uniform_lengths(2000, 4, 16)
+    off = offsets_for(lengths)
+    n = int(off[-1])
+    t = torch.zeros(n, dtype=torch.int64, device="cuda")
+    d_off = torch.from_numpy(off.view(np.int64).copy()).cuda()
+    stream = torch.cuda.Stream()
+    assert ips4o.ips4o_reserve_workspace(n, len(lengths), ips4o.U64, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        _async_sort(ips4o, t, d_off, len(lengths), "u64", stream)
+    for seed in (31, 32, 33):
+        a = inputs.u64_segments(lengths, "uniform", seed=seed)
+        t.copy_(torch.from_numpy(a.view(np.int64)))
+        g.replay()
+        torch.cuda.synchronize()
+        check_segments(t.cpu().numpy().view(np.uint64), a, off, "u64")
+    assert ips4o.ips4o_stream_status(stream.cuda_stream) == 0
