@@ -407,6 +407,11 @@ def run_batched(args):
         j = j1
     stream = torch.cuda.current_stream()
     ips4o.reset_params()
+    tuned = None
+    if args.autotune:
+        from paper_1705_02257_gb300 import autotune
+        tuned = autotune.tune("u64", classes=range(14, 21), dist=args.dist,
+                              scheduler=args.segment_scheduler or 1)
     if args.segment_scheduler:
         ips4o.set_params(segment_scheduler=args.segment_scheduler)
     off_host = np.ascontiguousarray(off)
@@ -525,6 +530,10 @@ def run_batched(args):
         "cpu_baseline": cpu, "e2e": None, "clocks": clk.summary(),
         "gpu_launches": stats["kernel_launches"] * args.steps,
         "output_sorted": sorted_ok, "oracle_sample_ok": oracle_ok, "oracle_sample_segments": int(len(sample)),
+        "autotuned": None if tuned is None else {
+            "classes": {c: r["chosen"] for c, r in tuned["results"].items()},
+            "default_vs_best_ms": {c: [round(r["default_ms"], 3), round(r["best_ms"], 3)]
+                                   for c, r in tuned["results"].items()}},
         "stats": {k: stats[k] for k in ("levels", "chunks", "subproblems", "blocks_moved", "base_case_buckets",
                                         "workspace_bytes")},
     }
@@ -664,6 +673,8 @@ def main():
     ap.add_argument("--batched-total-log2", type=int, default=0,
                     help="batched: draw arrays until this many keys (2^x) instead of --segments")
     ap.add_argument("--verify-segments", type=int, default=200, help="batched: arrays checked against the oracle")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched: tune leaves / alpha per size class first and sort with that table")
     ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2],
                     help="batched: 0 automatic, 1 level by level, 2 one CTA per array")
     args = ap.parse_args()

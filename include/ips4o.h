@@ -93,6 +93,30 @@ typedef struct {
                                ips4o_sort_segmented_async) */
 } ips4o_params;
 
+/* Parameters of the distribution steps per size class, as an autotuner picks
+ * them (the paper fixes k = 256 and alpha = 0.2 log n for its CPUs, Section
+ * 4.7; on the GPU the best choice depends on the subproblem size).  Entry c
+ * applies to subproblems of n elements with 2^c <= n < 2^(c+1):
+ *   leaves  number of leaves of the step (power of two in [4, 256]; 0 = the
+ *           library's rule: about 2n / base-case size, at most k_max);
+ *   alpha   oversampling factor (alpha * leaves <= 4096; 0 = the default).
+ * The table is process-wide and applies to ips4o_sort, the segmented and
+ * batched calls (both forms) and ips4o_sort_segmented_async, not to
+ * ips4o_partition or ips4o_sort_noalloc. */
+#define IPS4O_NUM_CLASSES 64
+typedef struct {
+    uint16_t leaves;
+    uint16_t alpha;
+} ips4o_class_params;
+
+/* Set entries [0, count) of the table (count <= IPS4O_NUM_CLASSES; the rest
+ * are reset to 0); NULL resets the whole table.  The device copy used by the
+ * segment scheduler is updated on the current device (call it once per
+ * device, not while a stream is being captured).  INVALID_ARG if an entry
+ * breaks the rules above (nothing is changed then). */
+ips4o_status ips4o_set_class_params(const ips4o_class_params* table, size_t count);
+ips4o_status ips4o_get_class_params(ips4o_class_params* out, size_t count);
+
 /* Counters of the last completed call on the calling thread's current device. */
 #define IPS4O_NUM_PHASES 8
 typedef struct {

@@ -25,7 +25,10 @@ std::map<std::pair<int, uintptr_t>, DeviceState*> g_states;
 ips4o_stats g_last_stats[64];
 ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0};
 thread_local char g_last_err[256] = {0};
+ips4o_class_params g_classes[IPS4O_NUM_CLASSES] = {};
 }  // namespace
+
+const ips4o_class_params* class_table() { return g_classes; }
 
 ips4o_params& global_params() { return g_params; }
 
@@ -370,6 +373,32 @@ ips4o_status ips4o_set_params(const ips4o_params* p) {
     if (p->alpha > 4095) return IPS4O_ERR_INVALID_ARG;
     if (p->segment_scheduler < 0 || p->segment_scheduler > 2) return IPS4O_ERR_INVALID_ARG;
     g_params = *p;
+    return IPS4O_OK;
+}
+
+ips4o_status ips4o_set_class_params(const ips4o_class_params* table, size_t count) {
+    if (count > IPS4O_NUM_CLASSES || (count > 0 && !table)) return IPS4O_ERR_INVALID_ARG;
+    ips4o_class_params t[IPS4O_NUM_CLASSES] = {};
+    for (size_t c = 0; table && c < count; ++c) {
+        const unsigned L = table[c].leaves, a = table[c].alpha;
+        if (L && (L < 4 || L > 256 || (L & (L - 1)))) return IPS4O_ERR_INVALID_ARG;
+        if (a && L && a * L > 4096) return IPS4O_ERR_INVALID_ARG;
+        t[c] = table[c];
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_mtx);
+        std::memcpy(g_classes, t, sizeof t);
+    }
+    ips4o_status rc = upload_class_table_u64(t);
+    if (rc == IPS4O_OK) rc = upload_class_table_f64(t);
+    if (rc == IPS4O_OK) rc = upload_class_table_pair(t);
+    return rc;
+}
+
+ips4o_status ips4o_get_class_params(ips4o_class_params* out, size_t count) {
+    if (!out || count > IPS4O_NUM_CLASSES) return IPS4O_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mtx);
+    std::memcpy(out, g_classes, count * sizeof(ips4o_class_params));
     return IPS4O_OK;
 }
 

@@ -377,8 +377,10 @@ struct Driver {
         for (; i < count; ++i) {
             const Task t = tasks[i];
             if (nsub >= caps.max_sub) break;
-            u32 K = partition ? k_max : leaves_for(t.n, base_cap, k_max);
+            const ips4o_class_params cp = class_table()[63 - __builtin_clzll(t.n)];
+            u32 K = partition ? k_max : (cp.leaves ? (u32)cp.leaves : leaves_for(t.n, base_cap, k_max));
             u32 alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
+            if (!partition && cp.alpha) alpha = cp.alpha;
             alpha = std::max<u32>(1, std::min<u32>(alpha, 4096 / K));
             u64 ns = std::max<u64>(1, (t.n + stripe_len - 1) / stripe_len);
             ns = std::min<u64>(ns, kMaxStripesPerSub);
@@ -670,6 +672,15 @@ ips4o_status sort_segments_t(DeviceState& st, void* d, const std::vector<Task>& 
     Driver<T> drv(st, s);
     if (global_params().segment_scheduler == 2) return drv.run_scheduler((typename T::elem_t*)d, segs);
     return drv.run_segments((typename T::elem_t*)d, segs);
+}
+
+template <class T>
+ips4o_status upload_class_table_t(const ips4o_class_params* t) {
+    unsigned short lv[64], al[64];
+    for (int c = 0; c < 64; ++c) { lv[c] = t[c].leaves; al[c] = t[c].alpha; }
+    IPS4O_CUDA(cudaMemcpyToSymbol(c_class_leaves, lv, sizeof lv));
+    IPS4O_CUDA(cudaMemcpyToSymbol(c_class_alpha, al, sizeof al));
+    return IPS4O_OK;
 }
 
 template <class T>

@@ -14,6 +14,7 @@ ips4o_status sort_segments_f64(DeviceState& st, void* d, const std::vector<Task>
 ips4o_status enqueue_segments_f64(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s) {
     return enqueue_segments_t<TF64>(st, d, (const u64*)d_off, count, s);
 }
+ips4o_status upload_class_table_f64(const ips4o_class_params* t) { return upload_class_table_t<TF64>(t); }
 ips4o_status sort_noalloc_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks) {
     return noalloc_sort_t<TF64>(st, d, n, s, tasks);
 }

@@ -57,6 +57,12 @@ ips4o_status enqueue_segments_f64(DeviceState& st, void* d, const uint64_t* d_of
 ips4o_status enqueue_segments_pair(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s);
 ips4o_status sort_segments_f64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
 ips4o_status sort_segments_pair(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+// Per size class leaves / alpha (0 = the default rule), indexed by floor(log2 n).
+const ips4o_class_params* class_table();
+ips4o_status upload_class_table_u64(const ips4o_class_params* t);
+ips4o_status upload_class_table_f64(const ips4o_class_params* t);
+ips4o_status upload_class_table_pair(const ips4o_class_params* t);
+
 // ips4o_sort_noalloc's level loop; tasks = 2 * kNoAllocMaxTasks entries
 constexpr size_t kNoAllocMaxTasks = 256;   // subproblems per level (n / 16Ki << 256)
 ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);

@@ -22,6 +22,10 @@
 
 namespace ips4o {
 
+// The size-class table (leaves, alpha) on the device; zero = default rule.
+static __constant__ unsigned short c_class_leaves[64];
+static __constant__ unsigned short c_class_alpha[64];
+
 // Work queue and per-CTA stacks of the scheduler (device memory).
 struct SegQueue {
     Task* tasks;        // [count] the arrays, largest first
@@ -184,8 +188,10 @@ __global__ void __launch_bounds__(SegCfg<T>::TPB, 1)
         // ---- one distribution step of [t.begin, t.begin + t.n) by this CTA
         if (tid == 0) {
             atomicAdd(&ws.ctr->next_count, 1u);        // the scheduler counts its distribution steps here
-            const u32 K_ = seg_leaves(t.n, (u64)T::kBaseSmall, k_max);
-            u32 alpha = 16;
+            const int cls = 63 - __clzll((long long)t.n);
+            u32 K_ = c_class_leaves[cls];
+            if (K_ == 0) K_ = seg_leaves(t.n, (u64)T::kBaseSmall, k_max);
+            u32 alpha = c_class_alpha[cls] ? c_class_alpha[cls] : 16u;
             if (alpha * K_ > 4096) alpha = 4096 / K_;
             SubDesc sd;
             sd.begin = t.begin;

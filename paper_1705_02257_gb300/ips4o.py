@@ -48,6 +48,13 @@ class Params(ctypes.Structure):
                 ("segment_scheduler", ctypes.c_int)]
 
 
+class ClassParams(ctypes.Structure):
+    _fields_ = [("leaves", ctypes.c_uint16), ("alpha", ctypes.c_uint16)]
+
+
+NUM_CLASSES = 64
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("n", ctypes.c_uint64), ("levels", ctypes.c_uint32), ("chunks", ctypes.c_uint32),
                 ("subproblems", ctypes.c_uint64), ("kernel_launches", ctypes.c_uint64),
@@ -95,6 +102,10 @@ def _load():
     lib.ips4o_set_params.argtypes = [ctypes.POINTER(Params)]
     lib.ips4o_get_params.restype = i32
     lib.ips4o_get_params.argtypes = [ctypes.POINTER(Params)]
+    lib.ips4o_set_class_params.restype = i32
+    lib.ips4o_set_class_params.argtypes = [ctypes.POINTER(ClassParams), sz]
+    lib.ips4o_get_class_params.restype = i32
+    lib.ips4o_get_class_params.argtypes = [ctypes.POINTER(ClassParams), sz]
     lib.ips4o_get_stats.restype = i32
     lib.ips4o_get_stats.argtypes = [ctypes.POINTER(Stats)]
     lib.ips4o_base_case_capacity.restype = sz
@@ -178,6 +189,24 @@ def ips4o_get_params() -> Params:
     if rc:
         raise Ips4oError(rc, "ips4o_get_params")
     return p
+
+
+def ips4o_set_class_params(table) -> int:
+    """table: sequence of (leaves, alpha) per size class floor(log2 n), or None to reset."""
+    if table is None:
+        return _lib.ips4o_set_class_params(None, 0)
+    arr = (ClassParams * NUM_CLASSES)()
+    for c, (leaves, alpha) in enumerate(table):
+        arr[c].leaves, arr[c].alpha = int(leaves), int(alpha)
+    return _lib.ips4o_set_class_params(arr, len(table))
+
+
+def ips4o_get_class_params():
+    arr = (ClassParams * NUM_CLASSES)()
+    rc = _lib.ips4o_get_class_params(arr, NUM_CLASSES)
+    if rc:
+        raise Ips4oError(rc, "ips4o_get_class_params")
+    return [(arr[c].leaves, arr[c].alpha) for c in range(NUM_CLASSES)]
 
 
 def ips4o_get_stats() -> Stats:

@@ -61,3 +61,12 @@ def test_base_case_capacity(lib):
     from paper_1705_02257_gb300 import ips4o
     assert ips4o.ips4o_base_case_capacity(ips4o.U64) == 16384
     assert ips4o.ips4o_base_case_capacity(ips4o.PAIR_U64) == 8192
+
+
+def test_class_params_validation(lib):
+    from paper_1705_02257_gb300 import ips4o
+    before = ips4o.ips4o_get_class_params()
+    assert ips4o.ips4o_set_class_params([(100, 1)]) == 1       # leaves not a power of two
+    assert ips4o.ips4o_set_class_params([(2, 1)]) == 1         # fewer than 4 leaves
+    assert ips4o.ips4o_set_class_params([(256, 17)]) == 1      # alpha * leaves > 4096
+    assert ips4o.ips4o_get_class_params() == before            # rejected tables change nothing
