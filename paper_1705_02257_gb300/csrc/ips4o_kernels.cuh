@@ -590,29 +590,45 @@ template <class T>
 struct PermuteCfg {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    static constexpr int TPB = 256;
+    static constexpr int TPB = 128;
     static constexpr int NW = TPB / 32;
     static constexpr int V = 16;                 // movers per warp (lanes 0..V-1)
+    static constexpr int MIN_CTAS = 3;           // per SM: 12 warps, 192 movers
     static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block copy
     static constexpr int MAX_MOVERS_PER_BUCKET = 64;
+    // block buffers of the warps, then one copy of the subproblem's tables
+    // shared by the CTA (all its warps move blocks of the same subproblem)
     static constexpr size_t off_buf = 0;                                          // E[NW][2][V][B]
     static constexpr size_t off_tree = off_buf + (size_t)NW * 2 * V * T::kBlock * sizeof(E);
-    static constexpr size_t off_spl = off_tree + (size_t)NW * kMaxLeaves * sizeof(K);
-    static constexpr size_t off_delim = off_spl + (size_t)NW * kMaxLeaves * sizeof(K);
-    static constexpr size_t off_gpre = off_delim + (size_t)NW * (kMaxBuckets + 1) * 4;
-    static constexpr size_t smem_bytes = off_gpre + 1025 * 4 + 64 * 8;
+    static constexpr size_t off_spl = off_tree + (size_t)kMaxLeaves * sizeof(K);
+    static constexpr size_t off_delim = off_spl + (size_t)kMaxLeaves * sizeof(K);
+    static constexpr size_t off_gpre = off_delim + (size_t)(kMaxBuckets + 4) * 4;   // u16[1025]
+    static constexpr size_t off_misc = off_gpre + 1032 * 2;
+    static constexpr size_t smem_bytes = off_misc + 40 * 8;
     static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
 };
 
+// Copy subproblem j's search tree, splitters and delimiters into shared
+// memory (all threads of the CTA take part).
+template <class T>
+__device__ __forceinline__ void load_sub_tables(const Workspace<T>& ws, u32 j, typename T::key_t* tree,
+                                                typename T::key_t* spl, u32* delim) {
+    for (int i = threadIdx.x; i < kMaxLeaves; i += blockDim.x) {
+        tree[i] = ws.tree[(u64)j * kMaxLeaves + i];
+        spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
+    }
+    for (int i = threadIdx.x; i <= kMaxBuckets; i += blockDim.x) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
+}
+
 // One mover group (a warp of V movers) of subproblem j: group gl of the
 // subproblem's groups, nmov movers in all (Section 4.2).  wbuf is the warp's
-// [2][V][b] block buffer; tree, spl, delim its copies of the subproblem's
-// search tree, splitters and delimiters (shared memory).
+// [2][V][b] block buffer; tree, spl, delim the subproblem's search tree,
+// splitters and delimiters in shared memory (load_sub_tables).
 template <class T>
 __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Workspace<T>& ws, u32 j, u32 gl,
-                                              u32 nmov, typename T::elem_t* wbuf, typename T::key_t* tree,
-                                              typename T::key_t* spl, u32* delim, u32 spin_limit, u64& moved,
-                                              u64& skipped, bool& failed) {
+                                              u32 nmov, typename T::elem_t* wbuf, const typename T::key_t* tree,
+                                              const typename T::key_t* spl, const u32* delim, u32 spin_limit,
+                                              u64& moved, u64& skipped, bool& failed) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
@@ -623,14 +639,6 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
     const u32 nb = sub.nbuckets;
     const int logL = (int)sub.log_leaves;
     const bool eq = sub.eq != 0;
-    // this warp's copy of the subproblem's tree, splitters and delimiters
-    __syncwarp();
-    for (int i = lane; i < kMaxLeaves; i += 32) {
-        tree[i] = ws.tree[(u64)j * kMaxLeaves + i];
-        spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
-    }
-    for (int i = lane; i <= kMaxBuckets; i += 32) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
-    __syncwarp();
     u64* wr = ws.wr + (u64)j * kMaxBuckets;
     u32* exh = ws.exhausted + (u64)j * 8;
     E* A = arr + sub.begin;
@@ -778,19 +786,20 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
 }
 
 template <class T>
-__global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
+__global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     k_permute(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 spin_limit) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
     constexpr int TPB = C::TPB, NW = C::NW, V = C::V, EPL = C::EPL, B = T::kBlock;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    u32* s_gpre = (u32*)(smem_raw + C::off_gpre);
-    u64* s_misc = (u64*)(smem_raw + C::off_gpre + 1025 * 4 + 4);   // [0] total, [1..33] scan tmp
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const bool is_mover = lane < V;
-    const u32 G = gridDim.x * NW;                 // warps in the grid
-    // mover groups (warps) per subproblem, in proportion to its full blocks
+    unsigned short* s_gpre = (unsigned short*)(smem_raw + C::off_gpre);
+    u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0] total, [1..33] scan tmp
+    const int warp = threadIdx.x >> 5;
+    const u32 G = gridDim.x;                      // CTAs in the grid
+    constexpr u32 MOV = (u32)NW * V;              // movers of one CTA
+    // CTAs per subproblem, in proportion to its full blocks; the warps of a
+    // CTA all work on one subproblem and share its tables
     u64 mine = 0;
     for (u32 i = threadIdx.x; i < nsub; i += TPB) mine += ws.subs[i].blocks_total;
     if (threadIdx.x == 0) s_misc[0] = 0;
@@ -810,9 +819,9 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
                 const u64 bl = sd.blocks_total;
                 if (bl > 0) {
                     u64 x = (bl * (u64)G + total - 1) / total;
-                    const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + V - 1) / V;
-                    const u64 cap_k = (bl + V - 1) / V;
-                    const u64 cap_r = kMaxMoversPerSub / V;
+                    const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + MOV - 1) / MOV;
+                    const u64 cap_k = (bl + MOV - 1) / MOV;
+                    const u64 cap_r = kMaxMoversPerSub / MOV;
                     x = x < cap_b ? x : cap_b;
                     x = x < cap_k ? x : cap_k;
                     x = x < cap_r ? x : cap_r;
@@ -826,26 +835,31 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, 1)
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const u32 i = threadIdx.x * PER + q;
-            if (i < nsub) s_gpre[i] = p;
+            if (i < nsub) s_gpre[i] = (unsigned short)p;
             p += gv[q];
         }
-        if (threadIdx.x == 0) s_gpre[nsub] = tot;
+        if (threadIdx.x == 0) s_gpre[nsub] = (unsigned short)tot;
         __syncthreads();
     }
     const u32 GT = s_gpre[nsub];
     E* wbuf = (E*)(smem_raw + C::off_buf) + (size_t)warp * 2 * V * B;   // [2][V][B]
-    K* tree = (K*)(smem_raw + C::off_tree) + (size_t)warp * kMaxLeaves;
-    K* spl = (K*)(smem_raw + C::off_spl) + (size_t)warp * kMaxLeaves;
-    u32* delim = (u32*)(smem_raw + C::off_delim) + (size_t)warp * (kMaxBuckets + 1);
+    K* tree = (K*)(smem_raw + C::off_tree);
+    K* spl = (K*)(smem_raw + C::off_spl);
+    u32* delim = (u32*)(smem_raw + C::off_delim);
     u64 moved = 0, skipped = 0;
     bool failed = false;
-    for (u32 g = blockIdx.x * NW + warp; g < GT && !failed; g += G) {
+    for (u32 g = blockIdx.x; g < GT; g += G) {
         u32 lo = 0, hi = nsub;
         while (hi - lo > 1) { u32 mid = (lo + hi) >> 1; if (s_gpre[mid] <= g) lo = mid; else hi = mid; }
         const u32 j = lo;
-        const u32 gl = g - s_gpre[j];
-        const u32 nmov = (s_gpre[j + 1] - s_gpre[j]) * V;
-        permute_group<T>(arr, ws, j, gl, nmov, wbuf, tree, spl, delim, spin_limit, moved, skipped, failed);
+        const u32 cl = g - s_gpre[j];
+        const u32 nmov = (s_gpre[j + 1] - s_gpre[j]) * MOV;
+        __syncthreads();                          // the previous group is done with the tables
+        load_sub_tables<T>(ws, j, tree, spl, delim);
+        __syncthreads();
+        permute_group<T>(arr, ws, j, cl * NW + warp, nmov, wbuf, tree, spl, delim, spin_limit, moved, skipped,
+                         failed);
+        if (__syncthreads_or(failed)) break;
     }
     if (moved) atomicAdd(&ws.ctr->blocks_moved, moved);
     if (skipped) atomicAdd(&ws.ctr->blocks_skipped, skipped);

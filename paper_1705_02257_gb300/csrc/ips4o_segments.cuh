@@ -49,7 +49,7 @@ struct SegCfg {
     static constexpr size_t sample_bytes = 4096 * sizeof(K) + 256 * sizeof(K) + 32 * 4;
     static constexpr size_t prefix_bytes = 32 * 8 + 2 * kMaxStripesPerSub * 4 + (kMaxBuckets + 1) * 4;
     static constexpr size_t perm_buf = (size_t)NWP * 2 * PermuteCfg<T>::V * B * sizeof(E);
-    static constexpr size_t perm_bytes = perm_buf + (size_t)NWP * (2 * kMaxLeaves * sizeof(K) + (kMaxBuckets + 1) * 4);
+    static constexpr size_t perm_bytes = perm_buf + 2 * kMaxLeaves * sizeof(K) + (kMaxBuckets + 1) * 4;
     static constexpr size_t clean_bytes = (size_t)kMaxBuckets * B * sizeof(E);
     static constexpr size_t m1 = ClassifyCfg<T>::smem_bytes > Base::smem_bytes ? ClassifyCfg<T>::smem_bytes
                                                                                   : Base::smem_bytes;
@@ -230,13 +230,14 @@ __global__ void __launch_bounds__(SegCfg<T>::TPB, 1)
             prefix_sub<T, TPB>(ws, j, tmp64, s_sbk, s_full, s_delim);
         }
         // block permutation by the first NWP warps (Section 4.2)
+        K* tree = (K*)(smem_raw + C::perm_buf);
+        K* spl = tree + kMaxLeaves;
+        u32* delim = (u32*)(spl + kMaxLeaves);
+        load_sub_tables<T>(ws, j, tree, spl, delim);
+        __syncthreads();
         if (warp < C::NWP) {
             constexpr int V = PermuteCfg<T>::V;
             E* wbuf = (E*)smem_raw + (size_t)warp * 2 * V * B;
-            K* tree = (K*)(smem_raw + C::perm_buf) + (size_t)warp * 2 * kMaxLeaves;
-            K* spl = tree + kMaxLeaves;
-            u32* delim = (u32*)(smem_raw + C::perm_buf + (size_t)C::NWP * 2 * kMaxLeaves * sizeof(K)) +
-                         (size_t)warp * (kMaxBuckets + 1);
             if (ws.subs[j].blocks_total > 0)
                 permute_group<T>(arr, ws, j, (u32)warp, (u32)(C::NWP * V), wbuf, tree, spl, delim, spin_limit, moved,
                                  skipped, failed);
