@@ -443,7 +443,8 @@ struct Driver {
         u32 kmax_chunk = 1;
         for (u32 q = 0; q < nsub; ++q) kmax_chunk = std::max(kmax_chunk, h_subs[q].k_target);
         const u32 bstride = std::min<u32>(kMaxBuckets, kmax_chunk >= 4 ? kmax_chunk : 2 * kmax_chunk);
-        IPS4O_LAUNCH(5, (k_cleanup<T><<<nsub * bstride, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+        const u32 clgrid = (nsub * bstride + CleanupCfg<T>::WPC - 1) / CleanupCfg<T>::WPC;
+        IPS4O_LAUNCH(5, (k_cleanup<T><<<clgrid, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
                             d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u, rec_cap)));
         if (!partition) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
