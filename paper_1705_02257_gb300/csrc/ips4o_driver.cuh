@@ -211,6 +211,7 @@ struct Driver {
     u32 rec_cap;        // buckets larger than this recurse; smaller go to the base case
     u32 k_max;
     int permute_grid = 0;
+    u64 level_stripe_len = 0;   // stripe length of the level being planned
     int next_event = 0;
     struct Timed { int phase; int ev; };
     std::vector<Timed> timed;
@@ -364,13 +365,41 @@ struct Driver {
         return status_from(h_ctr->status);
     }
 
+    // Stripe length of a level: the classification CTAs (one per SM) take
+    // stripes dynamically, so the number of stripes should fill whole waves
+    // of SMs.  Stripes of a subproblem have equal length and never cross it,
+    // so with many subproblems the count is a sum of per-subproblem
+    // roundings: try 2, 3, ... stripes per SM (from the stripes_per_sm
+    // parameter on) and keep the count whose last wave is fullest, with a
+    // small charge for extra stripes (more partial buffers to clean up).
+    u64 pick_stripe_len(const Task* tasks, size_t count, u64 level_total) const {
+        const u64 B = T::kBlock;
+        const u64 sms = (u64)st.sms;
+        const int w0 = std::max(1, prm.stripes_per_sm);
+        u64 best_len = 0;
+        double best_score = -1e30;
+        for (int wv = w0; wv <= w0 + 6; ++wv) {
+            u64 len = std::max<u64>((level_total + wv * sms - 1) / (wv * sms), kMinStripe);
+            len = (len + B - 1) / B * B;
+            u64 total = 0;
+            for (size_t i = 0; i < count; ++i) {
+                u64 ns = std::max<u64>(1, (tasks[i].n + len - 1) / len);
+                total += std::min<u64>(ns, kMaxStripesPerSub);
+            }
+            const u64 waves = (total + sms - 1) / sms;
+            const double score = (double)total / (double)(waves * sms) - 0.02 * (wv - w0);
+            if (score > best_score + 1e-9) { best_score = score; best_len = len; }
+            if (len == kMinStripe) break;                 // shorter stripes are not allowed
+        }
+        return best_len;
+    }
+
     // Plan one chunk starting at tasks[i0]; returns the number of tasks taken.
     size_t plan_chunk(const Task* tasks, size_t count, size_t i0, u64 level_total, u32 level, bool partition,
                       u32* nsub_out, u32* nstripes_out) {
         const u64 B = T::kBlock;
-        const u64 target = (u64)std::max(1, prm.stripes_per_sm) * (u64)st.sms;
-        u64 stripe_len = std::max<u64>((level_total + target - 1) / target, kMinStripe);
-        stripe_len = (stripe_len + B - 1) / B * B;
+        if (i0 == 0) level_stripe_len = pick_stripe_len(tasks, count, level_total);
+        const u64 stripe_len = level_stripe_len;
         u32 nsub = 0, nstr = 0;
         u64 pool = 0;
         size_t i = i0;
