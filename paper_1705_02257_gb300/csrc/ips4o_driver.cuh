@@ -69,7 +69,10 @@ Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
     c.max_sub = (u32)std::min<u64>(1024, n / (cap + 1) + 1);
     c.max_stripes = (u32)std::min<u64>(4096, target + c.max_sub + 1);
     target = std::min<u64>(target, n / kMinStripe + 1);   // stripes are at least kMinStripe long
-    u64 pool = std::max<u64>(n / 32, target * kMaxBuckets * (B - 1));
+    // partial buffers: the stripes of a lower level round up per subproblem,
+    // so room for 1.5 times the target number of stripes keeps a level in
+    // one chunk (Theorem 2: O(k b t) extra space)
+    u64 pool = std::max<u64>(n / 16, 3 * target * kMaxBuckets * (B - 1) / 2);
     pool = std::min<u64>(pool, n + kMaxBuckets * B);
     // a chunk never holds more leftovers than its stripes' buffers
     pool = std::min<u64>(pool, (u64)c.max_stripes * kMaxBuckets * (B - 1));
@@ -177,6 +180,8 @@ ips4o_status set_kernel_attributes(DeviceState& st) {
                                     (int)ClassifyCfg<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)CleanupCfg<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)CleanupCtaCfg<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseSmall<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)BaseSmall<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -378,14 +383,20 @@ struct Driver {
         const int w0 = std::max(1, prm.stripes_per_sm);
         u64 best_len = 0;
         double best_score = -1e30;
-        for (int wv = w0; wv <= w0 + 6; ++wv) {
+        // a level split into several chunks anyway keeps the default
+        const int w1 = count <= caps.max_sub ? w0 + 6 : w0;
+        for (int wv = w0; wv <= w1; ++wv) {
             u64 len = std::max<u64>((level_total + wv * sms - 1) / (wv * sms), kMinStripe);
             len = (len + B - 1) / B * B;
-            u64 total = 0;
+            u64 total = 0, pool = 0;
             for (size_t i = 0; i < count; ++i) {
-                u64 ns = std::max<u64>(1, (tasks[i].n + len - 1) / len);
-                total += std::min<u64>(ns, kMaxStripesPerSub);
+                const u64 ns = std::min<u64>(std::max<u64>(1, (tasks[i].n + len - 1) / len), kMaxStripesPerSub);
+                total += ns;
+                pool += ns * std::min<u64>((u64)kMaxBuckets * (B - 1), len);
             }
+            // more stripes than the workspace holds would split the level
+            // into more chunks: only the first candidate may do that
+            if (wv > w0 && (total > caps.max_stripes || pool > caps.pool_cap)) break;
             const u64 waves = (total + sms - 1) / sms;
             const double score = (double)total / (double)(waves * sms) - 0.02 * (wv - w0);
             if (score > best_score + 1e-9) { best_score = score; best_len = len; }
@@ -472,9 +483,20 @@ struct Driver {
         u32 kmax_chunk = 1;
         for (u32 q = 0; q < nsub; ++q) kmax_chunk = std::max(kmax_chunk, h_subs[q].k_target);
         const u32 bstride = std::min<u32>(kMaxBuckets, kmax_chunk >= 4 ? kmax_chunk : 2 * kmax_chunk);
-        const u32 clgrid = (nsub * bstride + CleanupCfg<T>::WPC - 1) / CleanupCfg<T>::WPC;
-        IPS4O_LAUNCH(5, (k_cleanup<T><<<clgrid, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u, rec_cap)));
+        // a bucket gathers partial buffers from every stripe of its
+        // subproblem: with many stripes (the top level) a CTA per bucket,
+        // with few (the lower levels, many small buckets) a warp per bucket
+        u32 max_ns = 1;
+        for (u32 q = 0; q < nsub; ++q) max_ns = std::max(max_ns, h_subs[q].num_stripes);
+        if (max_ns > 16) {
+            IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<nsub * bstride, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
+                                                stream>>>(d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u,
+                                                          rec_cap)));
+        } else {
+            const u32 clgrid = (nsub * bstride + CleanupCfg<T>::WPC - 1) / CleanupCfg<T>::WPC;
+            IPS4O_LAUNCH(5, (k_cleanup<T><<<clgrid, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                                d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u, rec_cap)));
+        }
         if (!partition) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
                                 d, ws.base_small, &ws.ctr->base_small, ws.ctr)));

@@ -866,7 +866,8 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
 }
 
 // --------------------------------------------------------------- cleanup
-// One warp per (subproblem, bucket), taken in ticket order; WPC warps per CTA.
+// One warp per (subproblem, bucket), taken in ticket order; WPC warps per CTA
+// (subproblems with few stripes: the lower levels).
 template <class T>
 struct CleanupCfg {
     typedef typename T::elem_t E;
@@ -1003,6 +1004,162 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
     if (b == 0 && lane == 0) IPS4O_GUARD(ws.ctr, ws.subs[j].nbuckets <= bstride, ws.subs[j].nbuckets, bstride);
     E* s_ov = (E*)(smem_raw + C::off_ov) + (size_t)warp * C::B;
     cleanup_bucket_warp<T>(arr, ws, j, b, s_ov, spin_limit, partition_only, rec_cap);
+}
+
+// ------------------------------------------------- cleanup, CTA per bucket
+// For subproblems with many stripes (the top level), where a bucket gathers
+// partial buffers from hundreds of stripes: one CTA per bucket.
+template <class T>
+struct CleanupCtaCfg {
+    typedef typename T::elem_t E;
+    static constexpr int TPB = 256;
+    static constexpr int B = T::kBlock;
+    static constexpr size_t off_ov = 0;
+    static constexpr size_t off_lpre = off_ov + (size_t)B * sizeof(E);
+    static constexpr size_t off_src = off_lpre + (size_t)(kMaxStripesPerSub + 1) * 4 + 4;
+    static constexpr size_t smem_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
+};
+
+template <class T>
+__global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
+    k_cleanup_cta(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 bstride, u32 spin_limit, u32 partition_only,
+              u32 rec_cap) {
+    typedef typename T::elem_t E;
+    typedef CleanupCtaCfg<T> C;
+    constexpr int TPB = C::TPB, B = C::B;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    E* s_ov = (E*)(smem_raw + C::off_ov);
+    u32* s_lpre = (u32*)(smem_raw + C::off_lpre);
+    u64* s_src = (u64*)(smem_raw + C::off_src);
+    __shared__ u32 s_ticket, s_ok;
+    __shared__ u32 tmp[32];
+    if (threadIdx.x == 0) s_ticket = atomicAdd(&ws.ctr->ticket, 1u);
+    __syncthreads();
+    const u32 ticket = s_ticket;
+    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
+    // largest bucket count, in increasing bucket order within a subproblem
+    const u32 j = ticket / bstride, b = ticket % bstride;
+    if (j >= nsub) return;
+    const SubDesc sub = ws.subs[j];
+    const u32 nb = sub.nbuckets;
+    if (b == 0) IPS4O_GUARD(ws.ctr, nb <= bstride, nb, bstride);
+    if (b >= nb) return;
+    E* A = arr + sub.begin;
+    const u64* bstart = ws.bstart + (u64)j * (kMaxBuckets + 1);
+    const u64 Bb = bstart[b], Eb = bstart[b + 1];
+    const u32 d0 = ws.delim[(u64)j * (kMaxBuckets + 1) + b];
+    const u64 w = (u64)d0 + (u64)pk_w(ws.wr[(u64)j * kMaxBuckets + b]);
+    const u64 nbc = sub.n / B;
+    const bool partial = (sub.n % B) != 0;
+    const bool has_blocks = w > d0;
+    // the bucket's last full block went to the overflow block
+    const u32 ovf = (partial && has_blocks && w == nbc + 1) ? (u32)B : 0u;
+    const u64 P_lo = (u64)d0 * B;
+    const u64 P_hi = has_blocks ? (ovf ? nbc : w) * B : P_lo;    // end of its blocks in the array
+    const u32 ov = (u32)((has_blocks && P_hi > Eb) ? P_hi - Eb : 0);  // overshoot into the next head
+    bool bad = ov > (u32)B || Eb < Bb || Eb > sub.n;
+    // read the overshoot before the next bucket may overwrite its head
+    if (!bad)
+        for (u32 v = threadIdx.x; v < ov; v += TPB) s_ov[v] = A[Eb + v];
+    __threadfence();
+    __syncthreads();
+    u32* flags = ws.flags + (u64)j * kMaxBuckets;
+    if (threadIdx.x == 0) {
+        st_release(&flags[b], 1u);
+        // This bucket's head [Bb, d0 * b) lies in block slot d0 - 1, the last
+        // slot of the region of bucket x, the last bucket before this one
+        // whose region starts below d0 (buckets in between are smaller than a
+        // block and share d0).  Only x's blocks can overshoot into that slot,
+        // so the head may be written once x has read its overshoot.
+        const u32* dl = ws.delim + (u64)j * (kMaxBuckets + 1);
+        int x = (int)b - 1;
+        while (x >= 0 && dl[x] >= d0) --x;
+        u32 ok = 1;
+        if (x >= 0) {
+            u32 it = 0;
+            while (ld_acquire(&flags[x]) == 0) {
+                if (++it > spin_limit) { ok = 0; break; }
+                __nanosleep(32);
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) {
+        if (threadIdx.x == 0) set_status(ws.ctr, kStatusTimeout);
+        return;
+    }
+    // empty slots: head [Bb, min(P_lo, Eb)) and tail [P_hi, Eb)
+    const u64 head_hi = P_lo < Eb ? P_lo : Eb;
+    const u64 nh = head_hi > Bb ? head_hi - Bb : 0;
+    const u64 nt = (P_lo < Eb && P_hi < Eb) ? Eb - P_hi : 0;
+    // sources: overshoot, overflow block, partial buffers of all stripes
+    const u32 ns = sub.num_stripes, sb = sub.stripe_begin;
+    constexpr int PER = (kMaxStripesPerSub + TPB - 1) / TPB;
+    u32 lc[PER], lsum = 0;
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const u32 i = threadIdx.x * PER + q;
+        lc[q] = 0;
+        if (i < ns) {
+            const u64 si = (u64)(sb + i) * kMaxBuckets + b;
+            lc[q] = ws.counts[si] % B;
+            s_src[i] = ws.stripes[sb + i].pool_off + ws.lscan[si];
+        }
+        lsum += lc[q];
+    }
+    u32 ltot;
+    u32 lp = block_exclusive_scan<u32>(lsum, tmp, &ltot);
+#pragma unroll
+    for (int q = 0; q < PER; ++q) {
+        const u32 i = threadIdx.x * PER + q;
+        if (i < ns) s_lpre[i] = lp;
+        lp += lc[q];
+    }
+    if (threadIdx.x == 0) s_lpre[ns] = ltot;
+    __syncthreads();
+    const u64 nsrc = (u64)ov + ovf + ltot;
+    if (bad || nh + nt != nsrc) {
+        if (threadIdx.x == 0) set_status(ws.ctr, kStatusInternal);
+        return;
+    }
+    const E* ovb = ws.overflow + (u64)j * B;
+    for (u64 q = threadIdx.x; q < nsrc; q += TPB) {
+        E x;
+        if (q < ov) {
+            x = s_ov[q];
+        } else if (q < (u64)ov + ovf) {
+            x = ovb[q - ov];
+        } else {
+            const u32 rr = (u32)(q - ov - ovf);
+            u32 lo = 0, hi = ns;
+            while (hi - lo > 1) { u32 mid = (lo + hi) >> 1; if (s_lpre[mid] <= rr) lo = mid; else hi = mid; }
+            x = ws.pool[s_src[lo] + (rr - s_lpre[lo])];
+        }
+        const u64 dst = q < nh ? Bb + q : P_hi + (q - nh);
+        A[dst] = x;
+    }
+    __syncthreads();
+    if (partition_only) return;
+    const u64 size = Eb - Bb;
+    const bool is_eq = sub.eq && (b & 1);
+    if (is_eq || size < 2) return;
+    if (threadIdx.x == 0) {
+        // buckets up to the base-case capacity are sorted in shared memory by
+        // the base-case kernels that follow; larger ones recurse (Section 4)
+        const Task task{sub.begin + Bb, size};
+        if (size > (u64)rec_cap) {
+            const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
+            if (idx < ws.next_cap) ws.next_tasks[idx] = task;
+            else set_status(ws.ctr, kStatusCapacity);
+        } else if (size <= (u64)T::kBaseSmall) {
+            const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
+            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
+        } else {
+            const u32 idx = atomicAdd(&ws.ctr->base_large, 1u);
+            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_large[idx] = task;
+        }
+    }
 }
 
 }  // namespace ips4o
