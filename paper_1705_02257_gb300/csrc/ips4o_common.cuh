@@ -30,7 +30,7 @@ constexpr unsigned long long kClaimRead = 1ull - (1ull << kRdBits);   // readers
 constexpr unsigned long long kClaimWrite = 1ull << kWShift;          // w + 1
 constexpr unsigned long long kReadDone = ~0ull;                      // readers - 1
 constexpr unsigned long long kMaxRegionBlocks = (1ull << kRBits) - kRBias - 2;
-constexpr unsigned kMaxMoversPerSub = 12000;              // < 2^kRdBits concurrent readers
+constexpr unsigned kMaxMoversPerSub = 16000;              // < 2^kRdBits concurrent readers
 
 // Device status word bits.
 constexpr u32 kStatusTimeout = 1u;     // a bounded wait gave up
