@@ -91,6 +91,8 @@ typedef struct {
                                level by level, the faster of the two), 1 level by level across
                                all segments, 2 the segment scheduler (one CTA per array, as in
                                ips4o_sort_segmented_async) */
+    uint32_t spin_limit;    /* polls of every bounded device wait before it gives up and the call
+                               returns IPS4O_ERR_TIMEOUT; 0 selects the default (2^22, about 0.3 s) */
 } ips4o_params;
 
 /* Parameters of the distribution steps per size class, as an autotuner picks
@@ -264,6 +266,14 @@ ips4o_status ips4o_get_stats(ips4o_stats* out);
 size_t ips4o_base_case_capacity(int key_type);
 
 const char* ips4o_status_string(int status);
+
+/* Self-check of the failure path (no counterpart in the paper): runs, on
+ * `stream`, one device wait of the kind the sort uses (a bounded poll of a
+ * flag) on a flag that nothing sets, with the given poll limit.  Returns
+ * IPS4O_ERR_TIMEOUT when the wait gave up and reported it as the sort
+ * kernels do; the context stays usable.  Any other result means the check
+ * failed.  Uses a few bytes of device memory built into the library. */
+ips4o_status ips4o_check_bounded_wait(uint32_t spin_limit, void* stream);
 
 /* Text of the last CUDA error seen by the library (empty if none). */
 const char* ips4o_last_cuda_error(void);

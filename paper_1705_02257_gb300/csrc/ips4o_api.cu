@@ -17,13 +17,20 @@
 
 namespace ips4o {
 
+// Failure-path self-check: a flag that nothing sets and a status word.
+static __device__ unsigned g_probe[2];
+
+static __global__ void k_wait_probe(unsigned* words, unsigned spin_limit) {
+    if (threadIdx.x == 0 && !wait_flag_set(&words[0], spin_limit)) atomicOr(&words[1], kStatusTimeout);
+}
+
 namespace {
 std::mutex g_mtx;
 // one state (workspace, staging, stats) per (device, stream): calls on
 // different streams run side by side, calls on one stream are serialised
 std::map<std::pair<int, uintptr_t>, DeviceState*> g_states;
 ips4o_stats g_last_stats[64];
-ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0};
+ips4o_params g_params = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0, 0};
 thread_local char g_last_err[256] = {0};
 ips4o_class_params g_classes[IPS4O_NUM_CLASSES] = {};
 }  // namespace
@@ -365,7 +372,7 @@ ips4o_status ips4o_release_workspace(void) {
 ips4o_status ips4o_set_params(const ips4o_params* p) {
     std::lock_guard<std::mutex> lk(g_mtx);
     if (!p) {
-        g_params = ips4o_params{256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0};
+        g_params = ips4o_params{256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull, 0, 0};
         return IPS4O_OK;
     }
     if (p->k_max < 4 || p->k_max > 256 || (p->k_max & (p->k_max - 1)) != 0) return IPS4O_ERR_INVALID_ARG;
@@ -445,6 +452,28 @@ const char* ips4o_status_string(int s) {
 }
 
 const char* ips4o_last_cuda_error(void) { return g_last_err; }
+
+ips4o_status ips4o_check_bounded_wait(uint32_t spin_limit, void* stream) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_probe);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetSymbolAddress"); return IPS4O_ERR_CUDA; }
+    unsigned* words = (unsigned*)p;                 // [0] the flag nothing sets, [1] the status
+    cudaStream_t s = (cudaStream_t)stream;
+    e = cudaMemsetAsync(words, 0, 2 * sizeof(unsigned), s);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32, 0, s>>>(words, spin_limit);
+        e = cudaGetLastError();
+    }
+    unsigned status = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&status, words + 1, sizeof status, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "ips4o_check_bounded_wait"); return IPS4O_ERR_CUDA; }
+    if (status & kStatusTimeout) return IPS4O_ERR_TIMEOUT;
+    return status ? IPS4O_ERR_INTERNAL : IPS4O_OK;
+}
 
 ips4o_status ips4o_stream_status(void* stream) {
     cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

@@ -263,6 +263,17 @@ static __device__ __noinline__ void guard_fail(ChunkCounters* c, u32 line, u64 a
     }
     atomicOr(&c->status, kStatusInternal);
 }
+// Bounded wait until *flag becomes non-zero (acquire): true when it did,
+// false after spin_limit polls (the caller reports IPS4O_ERR_TIMEOUT).
+__device__ __forceinline__ bool wait_flag_set(const u32* flag, u32 spin_limit) {
+    u32 it = 0;
+    while (ld_acquire(flag) == 0) {
+        if (++it > spin_limit) return false;
+        __nanosleep(32);
+    }
+    return true;
+}
+
 #define IPS4O_GUARD(ctr, cond, a, b) ((cond) ? true : (guard_fail((ctr), __LINE__, (u64)(a), (u64)(b)), false))
 
 // Bucket of key e (Section 3): descend the implicit tree a[1..L-1]

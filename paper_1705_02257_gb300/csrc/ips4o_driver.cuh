@@ -331,6 +331,8 @@ struct Driver {
         if (rc_ != IPS4O_OK) return rc_;                          \
     } while (0)
 
+    u32 spin_limit() const { return prm.spin_limit ? prm.spin_limit : kSpinLimit; }
+
     ips4o_status status_from(u32 bits) {
         if (h_ctr->guard_hits) {
             char msg[160];
@@ -476,7 +478,7 @@ struct Driver {
         IPS4O_LAUNCH(2, (k_prefix<T, 256><<<nsub, 256, 0, stream>>>(ws, nsub)));
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nsub, kSpinLimit)));
+                            d, ws, nsub, spin_limit())));
         // one cleanup CTA per (subproblem, bucket).  A subproblem planned
         // with K >= 4 leaves has at most K buckets: without equality buckets
         // at most K leaves, with them at most K/2 leaves and K - 1 buckets.
@@ -490,12 +492,12 @@ struct Driver {
         for (u32 q = 0; q < nsub; ++q) max_ns = std::max(max_ns, h_subs[q].num_stripes);
         if (max_ns > 16) {
             IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<nsub * bstride, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
-                                                stream>>>(d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u,
+                                                stream>>>(d, ws, nsub, bstride, spin_limit(), partition ? 1u : 0u,
                                                           rec_cap)));
         } else {
             const u32 clgrid = (nsub * bstride + CleanupCfg<T>::WPC - 1) / CleanupCfg<T>::WPC;
             IPS4O_LAUNCH(5, (k_cleanup<T><<<clgrid, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                                d, ws, nsub, bstride, kSpinLimit, partition ? 1u : 0u, rec_cap)));
+                                d, ws, nsub, bstride, spin_limit(), partition ? 1u : 0u, rec_cap)));
         }
         if (!partition) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
@@ -603,7 +605,7 @@ struct Driver {
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
         const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
         IPS4O_LAUNCH(4, (k_segments<T><<<st.sms, SegCfg<T>::TPB, SegCfg<T>::smem_bytes, stream>>>(
-                            d, ws, sq, prm.seed, k_max, kSpinLimit)));
+                            d, ws, sq, prm.seed, k_max, spin_limit())));
         IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
         IPS4O_CUDA(cudaStreamSynchronize(stream));
         IPS4O_CUDA(cudaGetLastError());
@@ -635,7 +637,7 @@ struct Driver {
         IPS4O_LAUNCH(7, (k_seg_fill<<<g, 256, 0, stream>>>(d_off, num_segments, ws.hist, ws.init_tasks, ws.ctr)));
         const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
         IPS4O_LAUNCH(4, (k_segments<T><<<st.sms, SegCfg<T>::TPB, SegCfg<T>::smem_bytes, stream>>>(
-                            d, ws, sq, prm.seed, k_max, kSpinLimit)));
+                            d, ws, sq, prm.seed, k_max, spin_limit())));
         return IPS4O_OK;
     }
 

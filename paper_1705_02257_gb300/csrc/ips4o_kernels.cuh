@@ -923,13 +923,7 @@ __device__ __forceinline__ void cleanup_bucket_warp(typename T::elem_t* arr, con
         // a block and share d0): only x's blocks can overshoot into it
         int x = (int)b - 1;
         while (x >= 0 && dl[x] >= d0) --x;
-        if (x >= 0) {
-            u32 it = 0;
-            while (ld_acquire(&flags[x]) == 0) {
-                if (++it > spin_limit) { ok = 0; break; }
-                __nanosleep(32);
-            }
-        }
+        if (x >= 0 && !wait_flag_set(&flags[x], spin_limit)) ok = 0;
     }
     ok = __shfl_sync(0xffffffffu, ok, 0);
     if (!ok) {
@@ -1075,13 +1069,7 @@ __global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
         int x = (int)b - 1;
         while (x >= 0 && dl[x] >= d0) --x;
         u32 ok = 1;
-        if (x >= 0) {
-            u32 it = 0;
-            while (ld_acquire(&flags[x]) == 0) {
-                if (++it > spin_limit) { ok = 0; break; }
-                __nanosleep(32);
-            }
-        }
+        if (x >= 0 && !wait_flag_set(&flags[x], spin_limit)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

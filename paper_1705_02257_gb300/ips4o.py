@@ -45,7 +45,7 @@ class Ips4oError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("alpha", ctypes.c_int), ("base_case_max", ctypes.c_int),
                 ("stripes_per_sm", ctypes.c_int), ("profile", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("segment_scheduler", ctypes.c_int)]
+                ("segment_scheduler", ctypes.c_int), ("spin_limit", ctypes.c_uint32)]
 
 
 class ClassParams(ctypes.Structure):
@@ -112,6 +112,8 @@ def _load():
     lib.ips4o_base_case_capacity.argtypes = [i32]
     lib.ips4o_status_string.restype = ctypes.c_char_p
     lib.ips4o_status_string.argtypes = [i32]
+    lib.ips4o_check_bounded_wait.restype = i32
+    lib.ips4o_check_bounded_wait.argtypes = [ctypes.c_uint32, vp]
     lib.ips4o_last_cuda_error.restype = ctypes.c_char_p
     lib.ips4o_last_cuda_error.argtypes = []
     return lib
@@ -223,6 +225,10 @@ def ips4o_base_case_capacity(key_type: int) -> int:
 
 def ips4o_status_string(status: int) -> str:
     return _lib.ips4o_status_string(status).decode()
+
+
+def ips4o_check_bounded_wait(spin_limit: int, stream: int = 0) -> int:
+    return _lib.ips4o_check_bounded_wait(spin_limit, stream)
 
 
 def last_cuda_error() -> str:
