@@ -36,6 +36,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "keys/s"
+# DRAM bytes per launch of the dominant kernels for 2^28 Uniform u64 keys: one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the same
+# kernels at 2^26 keys, where a launch processes a quarter of the elements,
+# scaled by 4 (averaged over the two distribution levels).  Retake the
+# capture when one of these kernels changes.
+TRAFFIC_2P28_U64_UNIFORM = {"classify": 4.048e9, "block_permutation": 3.936e9, "base_case": 4.054e9}
 ELEM_BYTES = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100}
 DTYPE_NAME = {"u64": "u64", "f64": "f64", "pair": "u64 key + u64 payload", "rec100": "80-bit byte key + 90-byte payload"}
 KT_LABEL = {"u64": "uint64 keys", "f64": "float64 keys", "pair": "16-byte (uint64 key, uint64 payload) pairs",
@@ -279,9 +285,12 @@ def run_gpu(args):
     alg = {
         "classify": per_level,
         "block_permutation": per_level,
-        "cleanup_base_case": 2.0 * n * dist_elem * prof_steps,
+        "base_case": 2.0 * n * dist_elem * prof_steps,
     }
     dominant = max(alg, key=lambda p: phase_ms[p])
+    traffic = None
+    if kt == "u64" and args.log2n == 28 and args.dist == "uniform":
+        traffic = TRAFFIC_2P28_U64_UNIFORM.get(dominant)
     peak, peak_kind = _peaks()
     achieved = alg[dominant] / (phase_ms[dominant] * 1e-3) / 1e9 if phase_ms[dominant] > 0 else None
     ms_per_step = total_ms / args.steps
@@ -336,9 +345,11 @@ def run_gpu(args):
         "roofline": {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak,
                      "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None,
-                     "traffic": None,
-                     "alg_bytes_per_launch": alg[dominant] / max(1, phase_launches[dominant]),
-                     "launches": phase_launches[dominant] // prof_steps,
+                     "traffic": traffic,
+                     "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the same "
+                                        "kernels at 2^26 keys, scaled by 4 to 2^28") if traffic else None,
+                     "alg_bytes_per_launch": alg[dominant] / (prof_steps * (levels if dominant != "base_case" else 1)),
+                     "launches": levels if dominant != "base_case" else 1,
                      "sort_alg_bytes": alg_sort, "sort_frac": sort_frac},
         "phase_ms_per_step": {p: phase_ms[p] / prof_steps for p in ips4o.PHASES},
         "cpu_baseline": cpu,

@@ -135,8 +135,8 @@ typedef struct {
     uint64_t workspace_bytes;      /* device workspace held by the library on this device */
     double phase_ms[IPS4O_NUM_PHASES]; /* with params.profile: summed kernel time per phase:
                                       0 sample, 1 classify, 2 prefix, 3 empty-block fix,
-                                      4 block permutation, 5 cleanup + base case,
-                                      6 standalone base case, 7 other */
+                                      4 block permutation (and the segment scheduler),
+                                      5 cleanup, 6 base case, 7 other */
     uint64_t phase_launches[IPS4O_NUM_PHASES];
 } ips4o_stats;
 

@@ -28,7 +28,7 @@ STATUS = {
     6: "IPS4O_ERR_TIMEOUT", 7: "IPS4O_ERR_INTERNAL", 8: "IPS4O_ERR_TOO_LARGE",
 }
 PHASES = ("sample", "classify", "prefix", "empty_block_fix", "block_permutation",
-          "cleanup_base_case", "base_case", "other")
+          "cleanup", "base_case", "other")
 
 
 class Ips4oError(RuntimeError):
