@@ -177,7 +177,7 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
 template <class T>
 ips4o_status set_kernel_attributes(DeviceState& st) {
     IPS4O_CUDA(cudaFuncSetAttribute(k_classify<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)ClassifyCfg<T>::smem_bytes));
+                                    (int)ClassifyRegCfg<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)CleanupCfg<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -474,7 +474,8 @@ struct Driver {
         const u64 seed = prm.seed;
         IPS4O_LAUNCH(0, (k_sample<T, 512><<<nsub, 512, 0, stream>>>(d, ws, nsub, seed)));
         const int cgrid = (int)std::min<u32>(nstr, (u32)st.sms);
-        IPS4O_LAUNCH(1, (k_classify<T><<<cgrid, ClassifyCfg<T>::TPB, ClassifyCfg<T>::smem_bytes, stream>>>(d, ws, nstr)));
+        IPS4O_LAUNCH(1, (k_classify<T><<<cgrid, ClassifyRegCfg<T>::TPB, ClassifyRegCfg<T>::smem_bytes, stream>>>(
+                            d, ws, nstr)));
         IPS4O_LAUNCH(2, (k_prefix<T, 256><<<nsub, 256, 0, stream>>>(ws, nsub)));
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(

@@ -112,6 +112,34 @@ struct ClassifyCfg {
     static_assert(TILE % TPB == 0, "tile must be a multiple of the CTA size");
 };
 
+template <class T>
+struct ClassifyRegCfg {
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
+    static constexpr int TPB = 512;
+    static constexpr int NW = TPB / 32;
+    static constexpr int TILE = 65536 / (int)sizeof(E);        // 64 KiB per tile
+    static constexpr int IPT = TILE / TPB;
+    static constexpr int B = T::kBlock;
+    static constexpr int MAXBLK = 384;                        // >= (256*(B-1) + TILE) / B
+    static constexpr size_t off_buf = 0;
+    static constexpr size_t off_grp = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
+    static constexpr size_t off_tree = off_grp + (size_t)TILE * sizeof(E);
+    static constexpr size_t off_spl = off_tree + kMaxLeaves * sizeof(K);
+    static constexpr size_t off_fill = off_spl + kMaxLeaves * sizeof(K);
+    static constexpr size_t off_cnt = off_fill + kMaxBuckets * 4;
+    static constexpr size_t off_off = off_cnt + kMaxBuckets * 4;
+    static constexpr size_t off_bscan = off_off + kMaxBuckets * 4;
+    static constexpr size_t off_total = off_bscan + kMaxBuckets * 4;
+    static constexpr size_t off_blkb = off_total + kMaxBuckets * 4;
+    static constexpr size_t off_emit = off_blkb + MAXBLK * 2;
+    static constexpr size_t off_misc = off_emit + kMaxBuckets * 2;
+    static constexpr size_t smem_bytes = off_misc + 64 * 8;
+    static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
+    static_assert(MAXBLK < 65536 && TILE < (1 << 30), "packed scan fields");
+    static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
+};
+
 // Bucket ids of IPT keys, descending the tree level by level for all keys at
 // once so that the IPT independent shared-memory lookups overlap.  LOGL is
 // the tree depth (log2 of the number of leaves), fixed at compile time.
@@ -366,8 +394,188 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
     }
 }
 
+// The same local classification with larger tiles held in registers
+// (ClassifyRegCfg<T>::TPB threads): each thread keeps IPT elements of the
+// current tile and loads its elements of the next tile while the current one
+// is classified and distributed, so shared memory needs no input staging
+// and holds one grouping area for the elements of buckets that emit blocks.
+// Twice the elements per tile halve the barriers per element.
 template <class T>
-__global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
+__device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>& ws, u32 s,
+                                    unsigned char* smem_raw) {
+    typedef ClassifyRegCfg<T> C;
+    typedef typename T::elem_t E;
+    typedef typename T::key_t K;
+    constexpr int TPB = C::TPB, NW = C::NW, TILE = C::TILE, IPT = C::IPT, B = C::B;
+    E* buf = (E*)(smem_raw + C::off_buf);
+    E* grp = (E*)(smem_raw + C::off_grp);          // grouping area of the emitting buckets
+    K* s_tree = (K*)(smem_raw + C::off_tree);
+    K* s_spl = (K*)(smem_raw + C::off_spl);
+    u32* s_fill = (u32*)(smem_raw + C::off_fill);
+    u32* s_cnt = (u32*)(smem_raw + C::off_cnt);
+    u32* s_off = (u32*)(smem_raw + C::off_off);     // grouped-tile offset of a bucket that fills a block
+    u32* s_bscan = (u32*)(smem_raw + C::off_bscan);
+    u32* s_total = (u32*)(smem_raw + C::off_total);
+    unsigned short* s_blkb = (unsigned short*)(smem_raw + C::off_blkb);
+    unsigned short* s_emit = (unsigned short*)(smem_raw + C::off_emit);   // buckets emitting in this tile
+    u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    {
+        const StripeDesc sd = ws.stripes[s];
+        const SubDesc sub = ws.subs[sd.sub];
+        const int logL = (int)sub.log_leaves;
+        const bool eq = sub.eq != 0;
+        u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
+        u32* s_tlo = s_thi + kMaxLeaves;
+        for (int i = tid; i < kMaxLeaves; i += TPB) {
+            const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
+            s_thi[i] = (u32)(a >> 32);
+            s_tlo[i] = (u32)a;
+            s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
+        }
+        for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
+        E* A = arr + sd.begin;
+        const u32 len = (u32)(sd.end - sd.begin);   // a stripe holds < 2^32 elements
+        const u32 ntiles = (len + TILE - 1) / TILE;
+        u32 front = 0;                       // full blocks written at the stripe front
+        __syncthreads();
+
+        E nx[IPT];
+        auto load_tile = [&](u32 tn) {
+            const u32 tb = tn * TILE;
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const u32 idx = tid + q * TPB;
+                if (tb + idx < len) nx[q] = A[tb + idx];
+            }
+        };
+        if (ntiles > 0) load_tile(0);
+        for (u32 t = 0; t < ntiles; ++t) {
+            E e[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) e[q] = nx[q];
+            // the next tile's loads stay in flight while this one is processed
+            if (t + 1 < ntiles) load_tile(t + 1);
+            E* tile = grp;
+            const u32 tb = t * TILE;
+            const u32 tcount = len - tb < (u32)TILE ? len - tb : (u32)TILE;
+            K k[IPT];
+            int bk[IPT];
+            u32 rk[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
+            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                if (tid + q * TPB >= tcount) bk[q] = -1;
+                // rank within the tile's run of the bucket; a warp whose lanes
+                // all hit one bucket (long runs, repeated keys) takes one atomic
+                const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
+                if (__all_sync(0xffffffffu, bk[q] == b0)) {
+                    u32 base = 0;
+                    if (lane == 0 && b0 >= 0) base = atomicAdd(&s_cnt[b0], 32u);
+                    rk[q] = __shfl_sync(0xffffffffu, base, 0) + lane;
+                } else {
+                    rk[q] = bk[q] >= 0 ? atomicAdd(&s_cnt[bk[q]], 1u) : 0u;
+                }
+            }
+            __syncthreads();
+            // Buckets whose buffer block fills in this tile emit full blocks;
+            // their new elements are grouped in the (now free) staging slot.
+            // The new elements of every other bucket go straight into its
+            // buffer block.
+            u32 c = 0, f = 0, nfull = 0;
+            if (tid < kMaxBuckets) {
+                c = s_cnt[tid];
+                f = s_fill[tid];
+                nfull = (f + c) / B;
+            }
+            // one scan of three packed counts: [tile offset 32 | blocks 16 | emitting buckets 16]
+            u64 tot;
+            const u64 pre = block_exclusive_scan<u64>(((u64)(nfull ? c : 0u) << 32) | ((u64)nfull << 16) |
+                                                          (nfull ? 1u : 0u),
+                                                      s_misc, &tot);
+            const u32 tot_blocks = (u32)((tot >> 16) & 0xffffu);
+            const u32 n_emit = (u32)(tot & 0xffffu);
+            if (tid < kMaxBuckets) {
+                const u32 bpre = (u32)((pre >> 16) & 0xffffu);
+                s_off[tid] = nfull ? (u32)(pre >> 32) : 0xffffffffu;
+                s_bscan[tid] = bpre;
+                for (u32 q = 0; q < nfull; ++q) s_blkb[bpre + q] = (unsigned short)tid;
+                if (nfull) s_emit[(u32)(pre & 0xffffu)] = (unsigned short)tid;
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                if (bk[q] >= 0) {
+                    const u32 ob = s_off[bk[q]];
+                    if (ob == 0xffffffffu) buf[bk[q] * B + s_fill[bk[q]] + rk[q]] = e[q];
+                    else tile[ob + rk[q]] = e[q];
+                }
+            }
+            __syncthreads();
+            // write full blocks over the front of the stripe
+            for (u32 i = warp; i < tot_blocks; i += NW) {
+                const u32 b = s_blkb[i];
+                const u32 jb = i - s_bscan[b];
+                const u32 fb = s_fill[b];
+                const u32 ob = s_off[b];
+                const u32 dst = (front + i) * B;
+                if (dst + B <= len) {
+                    E* g = A + dst;
+#pragma unroll
+                    for (int v = lane; v < B; v += 32) {
+                        const u32 vv = jb * B + v;
+                        g[v] = vv < fb ? buf[b * B + vv] : tile[ob + vv - fb];
+                    }
+                } else if (lane == 0) {
+                    set_status(ws.ctr, kStatusInternal);
+                }
+            }
+            __syncthreads();
+            // the remainder of a bucket that emitted blocks goes back into its
+            // buffer block (one warp per such bucket)
+            for (u32 i = warp; i < n_emit; i += NW) {
+                const u32 b = s_emit[i];
+                const u32 fb = s_fill[b], cb = s_cnt[b];
+                const u32 nf = (fb + cb) / B, rem = (fb + cb) % B;
+                const u32 from = s_off[b] + nf * B - fb;
+                for (u32 v = lane; v < rem; v += 32) buf[b * B + v] = tile[from + v];
+            }
+            __syncthreads();
+            if (tid < kMaxBuckets) {
+                s_total[tid] += c;
+                s_fill[tid] = (f + c) % B;
+                s_cnt[tid] = 0;
+            }
+            front += tot_blocks;
+            __syncthreads();
+        }
+        // counts, leftovers (partially filled buffers) to the stripe's pool area
+        u32 f = tid < kMaxBuckets ? s_fill[tid] : 0;
+        u32 ltot;
+        u32 lpre = block_exclusive_scan<u32>(f, (u32*)s_misc, &ltot);
+        if (tid < kMaxBuckets) {
+            ws.counts[(u64)s * kMaxBuckets + tid] = s_total[tid];
+            ws.lscan[(u64)s * kMaxBuckets + tid] = lpre;
+            s_off[tid] = lpre;
+        }
+        __syncthreads();
+        if (ltot <= sd.pool_cap) {
+            for (int b = warp; b < kMaxBuckets; b += NW) {
+                const u32 fb = s_fill[b], ob = s_off[b];
+                for (u32 v = lane; v < fb; v += 32) ws.pool[sd.pool_off + ob + v] = buf[b * B + v];
+            }
+        } else if (tid == 0) {
+            set_status(ws.ctr, kStatusInternal);
+        }
+        if (tid == 0) ws.stripe_full[s] = front;
+        __syncthreads();
+    }
+}
+
+template <class T>
+__global__ void __launch_bounds__(ClassifyRegCfg<T>::TPB, 1)
     k_classify(typename T::elem_t* arr, Workspace<T> ws, u32 nstripes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ u32 s_stripe;
@@ -377,7 +585,7 @@ __global__ void __launch_bounds__(ClassifyCfg<T>::TPB, 1)
         const u32 s = s_stripe;
         __syncthreads();
         if (s >= nstripes) break;
-        classify_stripe<T>(arr, ws, s, smem_raw);
+        classify_stripe_reg<T>(arr, ws, s, smem_raw);
     }
 }
 
