@@ -111,9 +111,12 @@ struct BaseCfg {
     static_assert(MAXSUB % TPB == 0, "whole sub-bucket counters per thread");
 };
 
-// The two size classes: most buckets (at most kBaseSmall elements) are
-// sorted by 512-thread CTAs that fit two per SM; the rare larger ones (up to
-// kBaseCap) by 1024-thread CTAs.
+// The three size classes: buckets of at most kBaseTiny elements (the typical
+// bucket of a last distribution step) are sorted by 256-thread CTAs, four
+// per SM; up to kBaseSmall by 512-thread CTAs, two per SM; the rare larger
+// ones (up to kBaseCap) by 1024-thread CTAs.
+template <class T>
+using BaseTiny = BaseCfg<T, 256, T::kBaseTiny>;
 template <class T>
 using BaseSmall = BaseCfg<T, 512, T::kBaseSmall>;
 template <class T>
@@ -301,7 +304,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
 // tasks i = blockIdx.x, blockIdx.x + gridDim.x, ... of the list; the count is
 // read from device memory, so the launch does not depend on the host.
 template <class T, class C>
-__global__ void __launch_bounds__(C::TPB, (C::TPB <= 512 ? 2 : 1))
+__global__ void __launch_bounds__(C::TPB, (C::TPB <= 256 ? 4 : (C::TPB <= 512 ? 2 : 1)))
     k_base(typename T::elem_t* arr, const Task* tasks, const u32* count, ChunkCounters* ctr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const u32 n = *count;

@@ -48,6 +48,7 @@ struct TU64 {
     typedef u64 key_t;
     static constexpr int kId = 0;
     static constexpr int kBlock = 64;                 // 64 x 8 B = 512 B
+    static constexpr int kBaseTiny = 4096;             // base case size class sorted by 256-thread CTAs
     static constexpr int kBaseSmall = 8192;            // base case size class sorted by 512-thread CTAs
     static constexpr int kBaseCap = 16384;             // largest bucket sorted in shared memory (128 KiB)
     __host__ __device__ static inline key_t key(const elem_t& e) { return e; }
@@ -59,6 +60,7 @@ struct TF64 {
     typedef u64 key_t;      // order-preserving map of the bits
     static constexpr int kId = 1;
     static constexpr int kBlock = 64;
+    static constexpr int kBaseTiny = 4096;
     static constexpr int kBaseSmall = 8192;
     static constexpr int kBaseCap = 16384;
     __host__ __device__ static inline key_t key(const elem_t& e) {
@@ -77,6 +79,7 @@ struct TPair {
     typedef u64 key_t;
     static constexpr int kId = 2;
     static constexpr int kBlock = 32;                 // 32 x 16 B = 512 B
+    static constexpr int kBaseTiny = 2048;
     static constexpr int kBaseSmall = 4096;
     static constexpr int kBaseCap = 8192;
     __host__ __device__ static inline key_t key(const elem_t& e) { return e.k; }
@@ -133,6 +136,8 @@ struct ChunkCounters {
     u64 guard_a, guard_b;   // operands of the first failed guard
     u32 base_small;     // base-case tasks of the small size class
     u32 base_large;     // base-case tasks of the large size class
+    u32 base_tiny;      // base-case tasks of the tiny size class
+    u32 pad2;
     u64 blocks_moved;
     u64 blocks_skipped;
     u64 fix_blocks;
@@ -164,8 +169,9 @@ struct Workspace {
     Task* next_tasks;         // [next_cap]
     Task* base_small;         // [max_sub * 256] buckets for the small base case
     Task* base_large;         // [max_sub * 256] buckets for the large base case
+    Task* base_tiny;          // [max_sub * 256] buckets for the tiny base case
     Task* init_tasks;         // [init_cap]      segments sorted by the base case alone / scheduler queue
-    u32* init_count;          // [2]             small / large entries of init_tasks; queue length, cursor
+    u32* init_count;          // [4]             tiny / small / large entries of init_tasks; queue length, cursor
     u32* hist;                // [65]            scheduler queue built on the device: size groups
     Task* stacks;             // [max_sub][stack_cap] scheduler: buckets each CTA still has to distribute
     ChunkCounters* ctr;       // [1]

@@ -118,9 +118,10 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.overflow = (E*)take(S * T::kBlock * sizeof(E));
     w.next_tasks = (Task*)take(c.next_cap * sizeof(Task));
     w.base_small = (Task*)take(S * kMaxBuckets * sizeof(Task));
+    w.base_tiny = (Task*)take(S * kMaxBuckets * sizeof(Task));
     w.base_large = (Task*)take(S * kMaxBuckets * sizeof(Task));
     w.init_tasks = (Task*)take(c.init_cap * sizeof(Task));
-    w.init_count = (u32*)take(2 * sizeof(u32));
+    w.init_count = (u32*)take(4 * sizeof(u32));
     w.hist = (u32*)take(65 * sizeof(u32));
     w.stacks = (Task*)take(S * c.stack_cap * sizeof(Task));
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
@@ -182,6 +183,8 @@ ips4o_status set_kernel_attributes(DeviceState& st) {
                                     (int)CleanupCfg<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_cleanup_cta<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)CleanupCtaCfg<T>::smem_bytes));
+    IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseTiny<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)BaseTiny<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseSmall<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)BaseSmall<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_base<T, BaseLarge<T>>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -350,13 +353,17 @@ struct Driver {
     ips4o_status base_only(E* d, u64 n) {
         h_tasks[0] = Task{0, n};
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
-        const bool small = n <= (u64)T::kBaseSmall;
-        Task* list = small ? ws.base_small : ws.base_large;
-        u32* cnt = small ? &ws.ctr->base_small : &ws.ctr->base_large;
+        const bool tiny = n <= (u64)T::kBaseTiny;
+        const bool small = !tiny && n <= (u64)T::kBaseSmall;
+        Task* list = tiny ? ws.base_tiny : (small ? ws.base_small : ws.base_large);
+        u32* cnt = tiny ? &ws.ctr->base_tiny : (small ? &ws.ctr->base_small : &ws.ctr->base_large);
         const u32 one = 1;
         IPS4O_CUDA(cudaMemcpyAsync(list, h_tasks, sizeof(Task), cudaMemcpyHostToDevice, stream));
         IPS4O_CUDA(cudaMemcpyAsync(cnt, &one, sizeof(u32), cudaMemcpyHostToDevice, stream));
-        if (small) {
+        if (tiny) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<1, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                                d, list, cnt, ws.ctr)));
+        } else if (small) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
                                 d, list, cnt, ws.ctr)));
         } else {
@@ -501,6 +508,8 @@ struct Driver {
                                 d, ws, nsub, bstride, spin_limit(), partition ? 1u : 0u, rec_cap)));
         }
         if (!partition) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<st.sms * 4, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                                d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<st.sms * 2, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
                                 d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
             IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<st.sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
@@ -545,30 +554,41 @@ struct Driver {
         ips4o_status rc = setup(total, nbase);
         if (rc != IPS4O_OK) return rc;
         st.stats.n = total;
-        std::vector<Task> init(nbase), big;
-        u32 nsmall = 0, nlarge = 0;
+        std::vector<Task> tiny, small, large, big;
         for (const Task& t : segs) {
             if (t.n < 2) continue;
             if (t.n > (u64)rec_cap) big.push_back(t);
-            else if (t.n <= (u64)T::kBaseSmall) init[nsmall++] = t;
-            else init[nbase - 1 - nlarge++] = t;
+            else if (t.n <= (u64)T::kBaseTiny) tiny.push_back(t);
+            else if (t.n <= (u64)T::kBaseSmall) small.push_back(t);
+            else large.push_back(t);
         }
         if (nbase > 0) {
-            const u32 cnt[2] = {nsmall, nlarge};
+            // init_tasks = tiny, then small, then large segments
+            std::vector<Task> init;
+            init.reserve(nbase);
+            init.insert(init.end(), tiny.begin(), tiny.end());
+            init.insert(init.end(), small.begin(), small.end());
+            init.insert(init.end(), large.begin(), large.end());
+            const u32 cnt[4] = {(u32)tiny.size(), (u32)small.size(), (u32)large.size(), 0u};
             // pageable sources: the copies have read them when the calls return
-            IPS4O_CUDA(cudaMemcpyAsync(ws.init_tasks, init.data(), nbase * sizeof(Task), cudaMemcpyHostToDevice,
+            IPS4O_CUDA(cudaMemcpyAsync(ws.init_tasks, init.data(), init.size() * sizeof(Task), cudaMemcpyHostToDevice,
                                        stream));
             IPS4O_CUDA(cudaMemcpyAsync(ws.init_count, cnt, sizeof cnt, cudaMemcpyHostToDevice, stream));
             IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
-            const int gsmall = (int)std::min<u64>(nsmall, (u64)st.sms * 2);
-            const int glarge = (int)std::min<u64>(nlarge, (u64)st.sms);
+            const int gtiny = (int)std::min<u64>(tiny.size(), (u64)st.sms * 4);
+            const int gsmall = (int)std::min<u64>(small.size(), (u64)st.sms * 2);
+            const int glarge = (int)std::min<u64>(large.size(), (u64)st.sms);
+            const Task* t_small = ws.init_tasks + tiny.size();
+            const Task* t_large = t_small + small.size();
+            if (gtiny > 0)
+                IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<gtiny, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes,
+                                                          stream>>>(d, ws.init_tasks, ws.init_count, ws.ctr)));
             if (gsmall > 0)
                 IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<gsmall, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes,
-                                                           stream>>>(d, ws.init_tasks, ws.init_count, ws.ctr)));
+                                                           stream>>>(d, t_small, ws.init_count + 1, ws.ctr)));
             if (glarge > 0)
                 IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<glarge, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes,
-                                                           stream>>>(d, ws.init_tasks + nsmall, ws.init_count + 1,
-                                                                     ws.ctr)));
+                                                           stream>>>(d, t_large, ws.init_count + 2, ws.ctr)));
             IPS4O_CUDA(cudaMemcpyAsync(h_ctr, ws.ctr, sizeof(ChunkCounters), cudaMemcpyDeviceToHost, stream));
             IPS4O_CUDA(cudaStreamSynchronize(stream));
             IPS4O_CUDA(cudaGetLastError());

@@ -1179,6 +1179,9 @@ __device__ __forceinline__ void cleanup_bucket_warp(typename T::elem_t* arr, con
         const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
         if (idx < ws.next_cap) ws.next_tasks[idx] = task;
         else set_status(ws.ctr, kStatusCapacity);
+    } else if (size <= (u64)T::kBaseTiny) {
+        const u32 idx = atomicAdd(&ws.ctr->base_tiny, 1u);
+        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_tiny[idx] = task;
     } else if (size <= (u64)T::kBaseSmall) {
         const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
         if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
@@ -1348,6 +1351,9 @@ __global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
             const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
             if (idx < ws.next_cap) ws.next_tasks[idx] = task;
             else set_status(ws.ctr, kStatusCapacity);
+        } else if (size <= (u64)T::kBaseTiny) {
+            const u32 idx = atomicAdd(&ws.ctr->base_tiny, 1u);
+            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_tiny[idx] = task;
         } else if (size <= (u64)T::kBaseSmall) {
             const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
             if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
