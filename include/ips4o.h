@@ -147,7 +147,10 @@ ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream);
 
 /* Same as ips4o_sort but for an array in HOST memory: copies it to the
  * device, sorts, and copies the result back (all on `stream`).  The device
- * staging buffer is owned by the library and kept for reuse. */
+ * staging buffer is owned by the library and kept for reuse.  For pinned
+ * host memory the copies are done by a kernel through the buffer's device
+ * address (the GPU reads and writes pinned host memory directly), else by
+ * cudaMemcpyAsync. */
 ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream);
 
 /* One distribution step (Section 4: sampling, local classification, block

@@ -24,6 +24,42 @@ static __global__ void k_wait_probe(unsigned* words, unsigned spin_limit) {
     if (threadIdx.x == 0 && !wait_flag_set(&words[0], spin_limit)) atomicOr(&words[1], kStatusTimeout);
 }
 
+// Copies between device memory and pinned host memory by a kernel: the GPU
+// reads and writes pinned host memory directly (over NVLink-C2C on a
+// Grace-Blackwell node, over PCIe elsewhere), and a grid of SMs keeps more
+// requests in flight than one copy engine.
+static __global__ void k_copy16(uint4* __restrict__ dst, const uint4* __restrict__ src, size_t n) {
+    // four independent 16-byte loads per thread in flight before the stores
+    constexpr int U = 4;
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; i + (U - 1) * stride < n; i += U * stride) {
+        uint4 v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = src[i + u * stride];
+#pragma unroll
+        for (int u = 0; u < U; ++u) dst[i + u * stride] = v[u];
+    }
+    for (; i < n; i += stride) dst[i] = src[i];
+}
+
+static __global__ void k_copy4(unsigned* __restrict__ dst, const unsigned* __restrict__ src, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// dst and src are device-accessible addresses; false if the alignment does
+// not allow a kernel copy (the caller then uses cudaMemcpyAsync).
+static bool kernel_copy(void* dst, const void* src, size_t bytes, cudaStream_t s, int sms, cudaError_t* err) {
+    const uintptr_t a = (uintptr_t)dst | (uintptr_t)src | (uintptr_t)bytes;
+    const int grid = sms * 16;
+    if (a % 16 == 0) k_copy16<<<grid, 256, 0, s>>>((uint4*)dst, (const uint4*)src, bytes / 16);
+    else if (a % 4 == 0) k_copy4<<<grid, 256, 0, s>>>((unsigned*)dst, (const unsigned*)src, bytes / 4);
+    else return false;
+    *err = cudaGetLastError();
+    return true;
+}
+
 namespace {
 std::mutex g_mtx;
 // one state (workspace, staging, stats) per (device, stream): calls on
@@ -288,12 +324,30 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
     rc = ensure_device_buffer(&st->d_host_copy, &st->d_host_copy_bytes, bytes);
     if (rc != IPS4O_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    e = cudaMemcpyAsync(st->d_host_copy, h_ptr, bytes, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(H2D)"); return IPS4O_ERR_CUDA; }
+    // pinned host memory: copy with a kernel through its device address
+    cudaPointerAttributes attr;
+    void* h_dev = nullptr;
+    if (cudaPointerGetAttributes(&attr, h_ptr) == cudaSuccess && attr.type == cudaMemoryTypeHost)
+        h_dev = attr.devicePointer;
+    cudaGetLastError();   // a plain pageable pointer may leave a query error behind
+    bool by_kernel = false;
+    if (h_dev) {
+        by_kernel = kernel_copy(st->d_host_copy, h_dev, bytes, s, st->sms, &e);
+        if (by_kernel && e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (H2D)"); return IPS4O_ERR_CUDA; }
+    }
+    if (!by_kernel) {
+        e = cudaMemcpyAsync(st->d_host_copy, h_ptr, bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(H2D)"); return IPS4O_ERR_CUDA; }
+    }
     rc = dispatch(*st, st->d_host_copy, n, key_type, s, nullptr);
     if (rc != IPS4O_OK) return rc;
-    e = cudaMemcpyAsync(h_ptr, st->d_host_copy, bytes, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(D2H)"); return IPS4O_ERR_CUDA; }
+    if (by_kernel) {
+        kernel_copy(h_dev, st->d_host_copy, bytes, s, st->sms, &e);
+        if (e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (D2H)"); return IPS4O_ERR_CUDA; }
+    } else {
+        e = cudaMemcpyAsync(h_ptr, st->d_host_copy, bytes, cudaMemcpyDeviceToHost, s);
+        if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(D2H)"); return IPS4O_ERR_CUDA; }
+    }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamSynchronize"); return IPS4O_ERR_CUDA; }
     return IPS4O_OK;
