@@ -281,7 +281,10 @@ def run_gpu(args):
     # block permutation each read and write the elements of the launch once.
     # Records are distributed as 16-byte (key prefix, index) pairs.
     dist_elem = 16 if kt == "rec100" else elem
-    per_level = 2.0 * n * dist_elem * levels * prof_steps
+    # elements classified over all levels of one sort (a deeper level often
+    # holds only a few buckets): the classification and permutation volume
+    distributed = stats["elements_distributed"] or n * levels
+    per_level = 2.0 * distributed * dist_elem * prof_steps
     alg = {
         "classify": per_level,
         "block_permutation": per_level,
@@ -295,7 +298,14 @@ def run_gpu(args):
     achieved = alg[dominant] / (phase_ms[dominant] * 1e-3) / 1e9 if phase_ms[dominant] > 0 else None
     ms_per_step = total_ms / args.steps
     value = n * world * args.steps / (total_ms * 1e-3)
-    alg_sort = (4 * levels + 2) * n * dist_elem
+    # the sort's roofline uses the nominal number of levels, log_k(n / base
+    # case) with k = 256, the same bar for every distribution
+    base_cap = ips4o.ips4o_base_case_capacity(ips4o.KEY_TYPES["pair" if kt == "rec100" else kt])
+    nominal_levels, m = 0, n
+    while m > base_cap:
+        m = (m + 255) // 256
+        nominal_levels += 1
+    alg_sort = (4 * nominal_levels + 2) * n * dist_elem
     if kt == "rec100":
         # key extraction (12 bytes read, 16 written), input copy (read + write)
         # and the gather (pair read, record read + write)
@@ -350,7 +360,8 @@ def run_gpu(args):
                                         "kernels at 2^26 keys, scaled by 4 to 2^28") if traffic else None,
                      "alg_bytes_per_launch": alg[dominant] / (prof_steps * (levels if dominant != "base_case" else 1)),
                      "launches": levels if dominant != "base_case" else 1,
-                     "sort_alg_bytes": alg_sort, "sort_frac": sort_frac},
+                     "alg_bytes_per_sort": alg[dominant] / prof_steps,
+                     "sort_alg_bytes": alg_sort, "sort_frac": sort_frac, "nominal_levels": nominal_levels},
         "phase_ms_per_step": {p: phase_ms[p] / prof_steps for p in ips4o.PHASES},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -660,7 +671,7 @@ def run_served(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dist", default="uniform")
