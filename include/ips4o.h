@@ -76,8 +76,10 @@ typedef enum {
 } ips4o_status;
 
 /* Tuning parameters (Section 4.7 gives k <= 256, alpha = 0.2 log n,
- * beta = 1, n0 = 16 and b = 2 KiB for its CPUs; the GPU defaults differ and
- * are explained in the design doc of the source distribution). */
+ * beta = 1, n0 = 16 and b = 2 KiB for its CPUs; the GPU defaults differ:
+ * 512-byte blocks so that the k buffer blocks of a classification CTA fit its
+ * shared memory, alpha = 16 because the shared-memory base case has a hard
+ * capacity, and a base case of up to 16 Ki elements instead of 16). */
 typedef struct {
     int k_max;            /* maximum buckets per distribution step, power of two in [4, 256]; default 256 */
     int alpha;            /* oversampling factor; <= 0 selects the default (max(8, 0.2 log2 n) ... see source) */
