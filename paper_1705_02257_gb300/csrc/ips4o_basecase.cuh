@@ -95,13 +95,17 @@ struct BaseCfg {
     static constexpr int NW = TPB / 32;
     static constexpr int CAP = CAP_;
     static constexpr int EPT = CAP / TPB;
-    static constexpr int N0 = 2;             // target sub-bucket size
+    static constexpr int N0 = 1;             // target sub-bucket size
     static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
     static constexpr int LIMIT = 64;         // larger sub-buckets are sorted one at a time by the CTA
     static constexpr int MAXBIG = CAP / LIMIT;
+    // sub-bucket counters/starts: entry s at pad(s) = s + s / 32, so that the
+    // SUBS_PER_THREAD consecutive entries each thread scans start in
+    // different banks for the 32 lanes of a warp
+    static constexpr u32 PADDED = MAXSUB + MAXSUB / 32 + 1;
     static constexpr size_t off_data = 0;
-    static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[MAXSUB + 1]
-    static constexpr size_t off_tmp = off_off + (MAXSUB + 1) * 4 + 12;
+    static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[PADDED]
+    static constexpr size_t off_tmp = off_off + ((size_t)PADDED * 4 + 15) / 16 * 16;
     static constexpr size_t off_big = off_tmp + 64 * 8;                     // u32[MAXBIG + 1]
     static constexpr size_t smem_bytes = off_big + (MAXBIG + 1) * 4;
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
@@ -109,6 +113,7 @@ struct BaseCfg {
     static_assert(CAP <= 65535, "ranks are packed in 16 bits");
     static_assert(EPT % 2 == 0, "ranks are packed two per register");
     static_assert(MAXSUB % TPB == 0, "whole sub-bucket counters per thread");
+    __device__ static __forceinline__ u32 pad(u32 s) { return s + (s >> 5); }
 };
 
 // The three size classes: buckets of at most kBaseTiny elements (the typical
@@ -156,7 +161,7 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 // Sort g[0..m), m <= CAP, with the whole CTA (BaseCfg<T>::TPB threads).
 //
 // The bucket is read once into registers.  Its key range [lo, hi] is split
-// into at most KB (about m / 4) sub-ranges of equal power-of-two width, and
+// into at most KB (about m / N0) sub-ranges of equal power-of-two width, and
 // every element goes to sub-bucket (key - lo) >> shift; a bucket produced by
 // the sampled distribution steps is close to uniform over its range, so the
 // sub-buckets are small.  After a
@@ -192,8 +197,8 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         }
     }
 #pragma unroll
-    for (int q = 0; q < SPT; ++q) off[tid * SPT + q] = 0;
-    if (tid == 0) { off[C::MAXSUB] = 0; big_list[0] = 0; }
+    for (int q = 0; q < SPT; ++q) off[C::pad(tid * SPT + q)] = 0;
+    if (tid == 0) { off[C::pad(C::MAXSUB)] = 0; big_list[0] = 0; }
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -233,36 +238,38 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
         if (idx < m) {
-            const u32 r = atomicAdd(&off[sub_of(T::key(e[q]))], 1u);
+            const u32 r = atomicAdd(&off[C::pad(sub_of(T::key(e[q])))], 1u);
             rk2[q / 2] |= r << (16 * (q & 1));
         }
     }
     __syncthreads();
     // exclusive scan of the sub-bucket sizes in place (SPT consecutive entries
-    // per thread); off[MAXSUB] receives the total
-    u32 c[SPT], csum = 0;
+    // per thread, read twice rather than held in registers); entry MAXSUB
+    // receives the total
+    u32 csum = 0;
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
-        c[q] = off[tid * SPT + q];
-        csum += c[q];
-        if (c[q] > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = tid * SPT + q;
+        const u32 cq = off[C::pad(tid * SPT + q)];
+        csum += cq;
+        if (cq > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = tid * SPT + q;
     }
     __syncthreads();
     u32 tot;
     u32 pre = block_exclusive_scan<u32>(csum, (u32*)tmp, &tot);
 #pragma unroll
     for (int q = 0; q < SPT; ++q) {
-        off[tid * SPT + q] = pre;
-        pre += c[q];
+        const u32 cq = off[C::pad(tid * SPT + q)];
+        off[C::pad(tid * SPT + q)] = pre;
+        pre += cq;
     }
-    if (tid == TPB - 1) off[C::MAXSUB] = pre;
+    if (tid == TPB - 1) off[C::pad(C::MAXSUB)] = pre;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
         if (idx < m) {
             const u32 r = (rk2[q / 2] >> (16 * (q & 1))) & 0xffffu;
-            data[off[sub_of(T::key(e[q]))] + r] = e[q];
+            data[off[C::pad(sub_of(T::key(e[q])))] + r] = e[q];
         }
     }
     __syncthreads();
@@ -275,7 +282,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
             const E x = data[i];
             const K k = T::key(x);
             const u32 sb = sub_of(k);
-            const u32 o = off[sb], o1 = off[sb + 1];
+            const u32 o = off[C::pad(sb)], o1 = off[C::pad(sb + 1)];
             if (o1 - o > (u32)C::LIMIT) continue;
             u32 r = 0;
             for (u32 jj = o; jj < o1; ++jj) {
@@ -288,7 +295,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     const u32 nbig = big_list[0];
     for (u32 q = 0; q < nbig; ++q) {
         const u32 sb = big_list[1 + q];
-        const u32 o = off[sb], len = off[sb + 1] - o;
+        const u32 o = off[C::pad(sb)], len = off[C::pad(sb + 1)] - o;
         // all keys equal: any order is sorted
         const K k0 = T::key(data[o]);
         int differs = 0;

@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 namespace ips4o {
@@ -52,6 +53,7 @@ struct TU64 {
     static constexpr int kBaseSmall = 8192;            // base case size class sorted by 512-thread CTAs
     static constexpr int kBaseCap = 16384;             // largest bucket sorted in shared memory (128 KiB)
     __host__ __device__ static inline key_t key(const elem_t& e) { return e; }
+    __host__ __device__ static inline elem_t unkey(const key_t& k) { return k; }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
 };
 
@@ -65,6 +67,9 @@ struct TF64 {
     static constexpr int kBaseCap = 16384;
     __host__ __device__ static inline key_t key(const elem_t& e) {
         return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
+    }
+    __host__ __device__ static inline elem_t unkey(const key_t& k) {   // inverse of key
+        return (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
     }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
 };
@@ -281,6 +286,102 @@ __device__ __forceinline__ bool wait_flag_set(const u32* flag, u32 spin_limit) {
 }
 
 #define IPS4O_GUARD(ctr, cond, a, b) ((cond) ? true : (guard_fail((ctr), __LINE__, (u64)(a), (u64)(b)), false))
+
+// ------------------------------------------------ splitter lookup table
+// A shortcut for the tree descent of Section 4.1 with the same result.
+// Let i(e) = #{t in [1, L-1] : s_t <= e} be the leaf index the descent
+// returns (s_1 <= ... <= s_{L-1}, the largest repeated as padding).  Keys
+// from s_1 upwards are mapped monotonically onto at most kLutCells cells
+// (linear cells of 2^shift keys over [s_1, s_{L-1}], the last one open
+// upwards, or logarithmic cells for keys spread over many orders of
+// magnitude); one more entry stands for the keys below s_1.  Entry c holds
+// lo_c = i(first key of cell c) and hi_c = i(first key of cell c + 1)
+// (L - 1 for the last cell), so that since i is non-decreasing every key e
+// of the cell has
+//     i(e) = lo_c + #{t in (lo_c, hi_c] : s_t <= e}.
+// Where the cells separate the splitters, most keys take one table lookup
+// and at most one comparison; cells with more splitters take a binary
+// search over (lo_c, hi_c].
+constexpr int kLutCells = 4096;
+constexpr int kLutBits = 12;                    // log2(kLutCells)
+constexpr int kLutMinLevels = 5;                // smaller trees keep the descent
+
+// Bit length of x (0 for x == 0).
+__host__ __device__ __forceinline__ u32 bitlen64(u64 x) {
+#ifdef __CUDA_ARCH__
+    return 64u - (u32)__clzll((long long)x);
+#else
+    u32 b = 0;
+    for (; x != 0; x >>= 1) ++b;
+    return b;
+#endif
+}
+
+// shift such that (top - base) >> shift < kLutCells (base <= top).
+__host__ __device__ __forceinline__ u32 lut_shift(u64 base, u64 top) {
+    const u32 bits = bitlen64(top - base);
+    return bits > (u32)kLutBits ? bits - (u32)kLutBits : 0u;
+}
+
+// Cell of key e: kLutCells for e < base, else min((e - base) >> shift, kLutCells - 1).
+__host__ __device__ __forceinline__ u32 lut_cell(u64 e, u64 base, u32 shift) {
+    const u64 d = (e - base) >> shift;
+    const u32 c = d < (u64)(kLutCells - 1) ? (u32)d : (u32)(kLutCells - 1);
+    return e < base ? (u32)kLutCells : c;
+}
+
+// First key of cell c (c < kLutCells); false when it lies above the key
+// domain (no key maps to the cell).
+__host__ __device__ __forceinline__ bool lut_cell_start(u32 c, u64 base, u32 shift, u64* start) {
+    const u64 off = (u64)c << shift;           // c < 2^12 and shift <= 52: no overflow
+    if (off > ~base) return false;
+    *start = base + off;
+    return true;
+}
+
+// Logarithmic cells for keys spread over many orders of magnitude: with
+// d = e - base, cell d for d < 2^(m+1), otherwise the bit length of d and
+// the m bits after its leading one, m = kLutLogMant (64 cells per octave,
+// 3776 cells for all of [0, 2^64)).  kLutCells again stands for e < base.
+constexpr u32 kLutLogMant = 6;
+__host__ __device__ __forceinline__ u32 lut_cell_log(u64 e, u64 base) {
+    const u64 d = e - base;
+    const u32 bl = bitlen64(d);
+    const u32 c = bl <= kLutLogMant + 1
+                      ? (u32)d
+                      : ((bl - kLutLogMant) << kLutLogMant) |
+                            (u32)((d >> (bl - 1 - kLutLogMant)) & ((1u << kLutLogMant) - 1));
+    return e < base ? (u32)kLutCells : c;
+}
+
+__host__ __device__ __forceinline__ bool lut_cell_start_log(u32 c, u64 base, u64* start) {
+    u64 off = c;
+    if (c >= (1u << kLutLogMant)) {
+        const u32 o = c >> kLutLogMant, mant = c & ((1u << kLutLogMant) - 1);
+        if (o + kLutLogMant > 64) return false;       // above every 64-bit d
+        off = (u64)((1u << kLutLogMant) | mant) << (o - 1);
+    }
+    if (off > ~base) return false;
+    *start = base + off;
+    return true;
+}
+
+// i(e) from the table entry (lo | hi << 8) and the sorted splitters spl[1..L-1].
+__host__ __device__ __forceinline__ int lut_refine(u64 e, u32 ent, const u64* spl) {
+    const int lo = (int)(ent & 0xffu), hi = (int)(ent >> 8);
+    const int nx = lo + 1 < kMaxLeaves ? lo + 1 : kMaxLeaves - 1;
+    int i = lo + ((hi > lo && spl[nx] <= e) ? 1 : 0);
+    if (hi > lo + 1) {
+        int a = lo, b = hi;                    // i(e) lies in [a, b]
+        while (a < b) {
+            const int m = (a + b + 1) >> 1;
+            if (spl[m] <= e) a = m;
+            else b = m - 1;
+        }
+        i = a;
+    }
+    return i;
+}
 
 // Bucket of key e (Section 3): descend the implicit tree a[1..L-1]
 // (a_1 = s_{L/2}, children of a_j are a_{2j}, a_{2j+1}) with j = 2j + (a_j <= e);

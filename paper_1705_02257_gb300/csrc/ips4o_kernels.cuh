@@ -134,10 +134,15 @@ struct ClassifyRegCfg {
     static constexpr size_t off_blkb = off_total + kMaxBuckets * 4;
     static constexpr size_t off_emit = off_blkb + MAXBLK * 2;
     static constexpr size_t off_misc = off_emit + kMaxBuckets * 2;
-    static constexpr size_t smem_bytes = off_misc + 64 * 8;
+    static constexpr size_t off_lut = off_misc + 64 * 8;    // u16[kLutCells + 1]: lo | hi << 8
+    static constexpr size_t off_dst = off_lut + (kLutCells + 8) * 2;   // u32[kMaxBuckets]
+    static constexpr size_t smem_bytes = off_dst + kMaxBuckets * 4;
+    static_assert(off_grp % sizeof(E) == 0 && off_buf == 0, "destinations count elements from the base");
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
     static_assert(MAXBLK < 65536 && TILE < (1 << 30), "packed scan fields");
     static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
+    static_assert(kLutCells % TPB == 0 && (size_t)TILE * sizeof(E) >= kLutCells, "table build layout");
+    static_assert(TILE <= 65536, "ranks are packed in 16 bits");
 };
 
 // Bucket ids of IPT keys, descending the tree level by level for all keys at
@@ -399,7 +404,10 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
 // current tile and loads its elements of the next tile while the current one
 // is classified and distributed, so shared memory needs no input staging
 // and holds one grouping area for the elements of buckets that emit blocks.
-// Twice the elements per tile halve the barriers per element.
+// Twice the elements per tile halve the barriers per element.  Keys are
+// classified through the splitter lookup table (lut_refine) where its cells
+// separate the splitters, else by the tree descent; the table is built once
+// per stripe from the subproblem's tree and gives the buckets of the descent.
 template <class T>
 __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>& ws, u32 s,
                                     unsigned char* smem_raw) {
@@ -419,6 +427,11 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
     unsigned short* s_blkb = (unsigned short*)(smem_raw + C::off_blkb);
     unsigned short* s_emit = (unsigned short*)(smem_raw + C::off_emit);   // buckets emitting in this tile
     u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp
+    unsigned short* s_lut = (unsigned short*)(smem_raw + C::off_lut);
+    // where the tile's next element of a bucket goes, in elements from the
+    // start of shared memory: its buffer block, or its grouping-area slot
+    u32* s_dst = (u32*)(smem_raw + C::off_dst);
+    E* s_elem = (E*)smem_raw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     {
         const StripeDesc sd = ws.stripes[s];
@@ -439,6 +452,54 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
         const u32 ntiles = (len + TILE - 1) / TILE;
         u32 front = 0;                       // full blocks written at the stripe front
         __syncthreads();
+        // The splitter lookup table.  Its cells are linear or logarithmic,
+        // whichever puts fewer pairs of adjacent distinct splitters into one
+        // cell (each such pair is a bucket whose keys all need the binary
+        // search); with more than L/16 such pairs either way, or a tree of
+        // fewer than kLutMinLevels levels (a few comparisons), the stripe
+        // keeps the tree descent.  lut_mode: 0 descent, 1 linear, 2 logarithmic.
+        const int L = 1 << logL;
+        const u64 lbase = s_spl[1], ltop = s_spl[L - 1];
+        const u32 lsh = lut_shift(lbase, ltop);
+        int lut_mode = 0;
+        {
+            int crowd_lin = 0, crowd_log = 0;
+            if (tid >= 1 && tid + 1 < L) {
+                const u64 a = s_spl[tid], b = s_spl[tid + 1];
+                if (a != b) {
+                    crowd_lin = lut_cell(a, lbase, lsh) == lut_cell(b, lbase, lsh) ? 1 : 0;
+                    crowd_log = lut_cell_log(a, lbase) == lut_cell_log(b, lbase) ? 1 : 0;
+                }
+            }
+            const int n_lin = __syncthreads_count(crowd_lin);
+            const int n_log = __syncthreads_count(crowd_log);
+            if (logL >= kLutMinLevels && (n_lin * 16 <= L || n_log * 16 <= L)) lut_mode = n_lin <= n_log ? 1 : 2;
+        }
+        if (lut_mode != 0) {
+            // i(first key of every cell) by the tree descent into the (still
+            // free) grouping area, then the (lo, hi) entries
+            constexpr int CPT = kLutCells / TPB;
+            unsigned char* s_lo = (unsigned char*)grp;
+            u64 ck[CPT];
+            int ci[CPT];
+            bool ok[CPT];
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const u32 c = (u32)(tid + q * TPB);
+                ok[q] = lut_mode == 1 ? lut_cell_start(c, lbase, lsh, &ck[q]) : lut_cell_start_log(c, lbase, &ck[q]);
+                if (!ok[q]) ck[q] = ltop;
+            }
+            classify_many<CPT>(ck, s_thi, s_tlo, s_spl, logL, false, ci);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) s_lo[tid + q * TPB] = (unsigned char)(ok[q] ? ci[q] : L - 1);
+            __syncthreads();
+            for (int c = tid; c <= kLutCells; c += TPB) {
+                u32 ent = 0;                          // cell kLutCells: keys below s_1
+                if (c < kLutCells) ent = (u32)s_lo[c] | ((c + 1 < kLutCells ? (u32)s_lo[c + 1] : (u32)(L - 1)) << 8);
+                s_lut[c] = (unsigned short)ent;
+            }
+            __syncthreads();
+        }
 
         E nx[IPT];
         auto load_tile = [&](u32 tn) {
@@ -459,25 +520,52 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
             E* tile = grp;
             const u32 tb = t * TILE;
             const u32 tcount = len - tb < (u32)TILE ? len - tb : (u32)TILE;
-            K k[IPT];
             int bk[IPT];
             u32 rk[IPT];
+            if (lut_mode == 1) {
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
-            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+                for (int q = 0; q < IPT; ++q) {
+                    const K kq = T::key(e[q]);
+                    const int i = lut_refine(kq, s_lut[lut_cell(kq, lbase, lsh)], s_spl);
+                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                }
+            } else if (lut_mode == 2) {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const K kq = T::key(e[q]);
+                    const int i = lut_refine(kq, s_lut[lut_cell_log(kq, lbase)], s_spl);
+                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                }
+            } else if constexpr (std::is_same<E, K>::value) {
+                // the keys replace the elements for the descent (one fewer
+                // register array), which the inverse map then restores
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) e[q] = T::key(e[q]);
+                classify_many<IPT>(e, s_thi, s_tlo, s_spl, logL, eq, bk);
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) e[q] = T::unkey(e[q]);
+            } else {
+                K k[IPT];
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
+                classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+            }
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (tid + q * TPB >= tcount) bk[q] = -1;
                 // rank within the tile's run of the bucket; a warp whose lanes
                 // all hit one bucket (long runs, repeated keys) takes one atomic
                 const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
+                u32 r;
                 if (__all_sync(0xffffffffu, bk[q] == b0)) {
                     u32 base = 0;
                     if (lane == 0 && b0 >= 0) base = atomicAdd(&s_cnt[b0], 32u);
-                    rk[q] = __shfl_sync(0xffffffffu, base, 0) + lane;
+                    r = __shfl_sync(0xffffffffu, base, 0) + lane;
                 } else {
-                    rk[q] = bk[q] >= 0 ? atomicAdd(&s_cnt[bk[q]], 1u) : 0u;
+                    r = bk[q] >= 0 ? atomicAdd(&s_cnt[bk[q]], 1u) : 0u;
                 }
+                // bucket and rank in one register: bucket << 16 | rank (rank < TILE)
+                rk[q] = bk[q] >= 0 ? ((u32)bk[q] << 16) | r : 0xffffffffu;
             }
             __syncthreads();
             // Buckets whose buffer block fills in this tile emit full blocks;
@@ -500,19 +588,15 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
             if (tid < kMaxBuckets) {
                 const u32 bpre = (u32)((pre >> 16) & 0xffffu);
                 s_off[tid] = nfull ? (u32)(pre >> 32) : 0xffffffffu;
+                s_dst[tid] = nfull ? (u32)(C::off_grp / sizeof(E)) + (u32)(pre >> 32) : (u32)tid * B + f;
                 s_bscan[tid] = bpre;
                 for (u32 q = 0; q < nfull; ++q) s_blkb[bpre + q] = (unsigned short)tid;
                 if (nfull) s_emit[(u32)(pre & 0xffffu)] = (unsigned short)tid;
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (bk[q] >= 0) {
-                    const u32 ob = s_off[bk[q]];
-                    if (ob == 0xffffffffu) buf[bk[q] * B + s_fill[bk[q]] + rk[q]] = e[q];
-                    else tile[ob + rk[q]] = e[q];
-                }
-            }
+            for (int q = 0; q < IPT; ++q)
+                if (rk[q] != 0xffffffffu) s_elem[s_dst[rk[q] >> 16] + (rk[q] & 0xffffu)] = e[q];
             __syncthreads();
             // write full blocks over the front of the stripe
             for (u32 i = warp; i < tot_blocks; i += NW) {

@@ -64,6 +64,26 @@ def test_u64_all_distributions_ragged_two_levels(ips4o, dist):
     check_u64(ips4o, inputs.u64(3_000_017, dist))
 
 
+def _key_range_case(kind, n):
+    u = inputs.u64(n, "uniform", seed=11)
+    v = inputs.u64(n, "uniform", seed=12)
+    if kind == "near_top":          # keys just below 2^64: cell starts past the top of the key domain
+        return (np.uint64(0xFFFFFFFFFFFFFFFF) - (u % np.uint64(100_000))).astype(np.uint64)
+    if kind == "mixed_scales":      # every magnitude: cells holding many splitters
+        return (u >> (v % np.uint64(64))).astype(np.uint64)
+    if kind == "clusters":          # 8 narrow clusters far apart
+        return (((v % np.uint64(8)) << np.uint64(60)) | (u % np.uint64(1000))).astype(np.uint64)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("n", [200_003, 3_000_017])
+@pytest.mark.parametrize("kind", ["near_top", "mixed_scales", "clusters"])
+def test_u64_key_range_corners(ips4o, kind, n):
+    # the splitter lookup table of the local classification: cells past the
+    # top of the domain, cells with many splitters, single-key cells
+    check_u64(ips4o, _key_range_case(kind, n))
+
+
 def test_u64_repeated_calls_same_result(ips4o):
     a = inputs.u64(500_001, "exponential")
     r1 = gpu_sort(ips4o, a, "u64")
@@ -118,7 +138,17 @@ def test_partition_bucket_rule(ips4o, kt, dist, n):
     """One distribution step: every bucket holds exactly the keys the
     splitters assign to it (Section 3, s_i <= e < s_{i+1}; Section 4.4,
     equality buckets hold one key), and the step permutes the input."""
-    a = inputs.make(kt, n, dist)
+    _check_partition(ips4o, inputs.make(kt, n, dist), kt)
+
+
+@pytest.mark.parametrize("n", [200_003, 3_000_017])
+@pytest.mark.parametrize("kind", ["near_top", "mixed_scales", "clusters"])
+def test_partition_bucket_rule_key_range_corners(ips4o, kind, n):
+    _check_partition(ips4o, _key_range_case(kind, n), "u64")
+
+
+def _check_partition(ips4o, a, kt):
+    n = len(a)
     raw = np.ascontiguousarray(a).view(np.uint8).reshape(-1)
     t = torch.from_numpy(raw.copy()).cuda()
     bounds, spl, eq = ips4o.partition(t, kt)
