@@ -662,6 +662,8 @@ struct Driver {
         return IPS4O_OK;
     }
 
+    static constexpr size_t kSortTasksMax = 1 << 16;   // host sort of a level's subproblems up to this many
+
     ips4o_status levels(E* d, std::vector<Task> level_tasks, PartitionOut* part) {
         ips4o_status rc = IPS4O_OK;
         std::vector<Task> next;
@@ -708,6 +710,11 @@ struct Driver {
                 return IPS4O_OK;
             }
             level_tasks.swap(next);
+            // larger subproblems first: their stripes are handed out first,
+            // so the dynamic stripe scheduler ends the level with short ones
+            if (level_tasks.size() <= kSortTasksMax)
+                std::sort(level_tasks.begin(), level_tasks.end(),
+                          [](const Task& a, const Task& b) { return a.n > b.n; });
             // guard against a runaway recursion (cannot happen: every level
             // shrinks every non-equality bucket)
             if (level > 64) return IPS4O_ERR_INTERNAL;
