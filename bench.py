@@ -41,7 +41,8 @@ METRIC = "keys/s"
 # kernels at 2^26 keys, where a launch processes a quarter of the elements,
 # scaled by 4 (averaged over the two distribution levels).  Retake the
 # capture when one of these kernels changes.
-TRAFFIC_2P28_U64_UNIFORM = {"classify": 4.045e9, "block_permutation": 3.937e9, "base_case": 3.81e9}
+NOMINAL_HBM_GBS = 7900.0      # the data-sheet HBM3e bandwidth, for context beside the measured peak
+TRAFFIC_2P28_U64_UNIFORM = {"classify": 4.046e9, "block_permutation": 3.936e9, "base_case": 3.811e9}
 ELEM_BYTES = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100}
 DTYPE_NAME = {"u64": "u64", "f64": "f64", "pair": "u64 key + u64 payload", "rec100": "80-bit byte key + 90-byte payload"}
 KT_LABEL = {"u64": "uint64 keys", "f64": "float64 keys", "pair": "16-byte (uint64 key, uint64 payload) pairs",
@@ -311,6 +312,12 @@ def run_gpu(args):
         # and the gather (pair read, record read + write)
         alg_sort += n * (12 + 16) + 2 * n * elem + n * (16 + 2 * elem)
     sort_frac = alg_sort / (ms_per_step * 1e-3) / 1e9 / peak
+    # the distribution levels alone (sampling through cleanup, no base case):
+    # 4 n s per nominal level over the device time of those phases
+    level_phases = ("sample", "classify", "prefix", "empty_block_fix", "block_permutation", "cleanup")
+    levels_ms = sum(phase_ms[p] for p in level_phases if p in phase_ms) / prof_steps
+    levels_alg = 4.0 * nominal_levels * n * dist_elem
+    levels_gbs = levels_alg / (levels_ms * 1e-3) / 1e9 if levels_ms > 0 else None
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     e2e = None
@@ -361,7 +368,10 @@ def run_gpu(args):
                      "alg_bytes_per_launch": alg[dominant] / (prof_steps * (levels if dominant != "base_case" else 1)),
                      "launches": levels if dominant != "base_case" else 1,
                      "alg_bytes_per_sort": alg[dominant] / prof_steps,
-                     "sort_alg_bytes": alg_sort, "sort_frac": sort_frac, "nominal_levels": nominal_levels},
+                     "sort_alg_bytes": alg_sort, "sort_frac": sort_frac, "nominal_levels": nominal_levels,
+                     "levels_alg_bytes": levels_alg, "levels_ms": levels_ms, "levels_gbs": levels_gbs,
+                     "levels_frac": (levels_gbs / peak) if levels_gbs else None,
+                     "levels_frac_of_nominal_7900": (levels_gbs / NOMINAL_HBM_GBS) if levels_gbs else None},
         "phase_ms_per_step": {p: phase_ms[p] / prof_steps for p in ips4o.PHASES},
         "cpu_baseline": cpu,
         "e2e": e2e,
