@@ -324,25 +324,38 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
     rc = ensure_device_buffer(&st->d_host_copy, &st->d_host_copy_bytes, bytes);
     if (rc != IPS4O_OK) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // pinned host memory: copy with a kernel through its device address
+    // pinned host memory is read and written by kernels through its device address
     cudaPointerAttributes attr;
     void* h_dev = nullptr;
     if (cudaPointerGetAttributes(&attr, h_ptr) == cudaSuccess && attr.type == cudaMemoryTypeHost)
         h_dev = attr.devicePointer;
     cudaGetLastError();   // a plain pageable pointer may leave a query error behind
     bool by_kernel = false;
-    if (h_dev) {
-        by_kernel = kernel_copy(st->d_host_copy, h_dev, bytes, s, st->sms, &e);
-        if (by_kernel && e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (H2D)"); return IPS4O_ERR_CUDA; }
+    if (h_dev && key_type != IPS4O_REC100_K10 && (uintptr_t)h_dev % elem_align(key_type) == 0) {
+        // pinned host memory and an element type sorted in place: the first
+        // distribution level reads the host buffer itself and writes its
+        // blocks into the device copy (no separate copy pass)
+        by_kernel = true;
+        switch (key_type) {
+        case IPS4O_U64: rc = sort_from_u64(*st, st->d_host_copy, h_dev, n, s); break;
+        case IPS4O_F64: rc = sort_from_f64(*st, st->d_host_copy, h_dev, n, s); break;
+        default: rc = sort_from_pair(*st, st->d_host_copy, h_dev, n, s); break;
+        }
+        publish_stats(*st);
+        if (rc != IPS4O_OK) return rc;
+    } else {
+        if (h_dev) {
+            by_kernel = kernel_copy(st->d_host_copy, h_dev, bytes, s, st->sms, &e);
+            if (by_kernel && e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (H2D)"); return IPS4O_ERR_CUDA; }
+        }
+        if (!by_kernel) {
+            e = cudaMemcpyAsync(st->d_host_copy, h_ptr, bytes, cudaMemcpyHostToDevice, s);
+            if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(H2D)"); return IPS4O_ERR_CUDA; }
+        }
+        rc = dispatch(*st, st->d_host_copy, n, key_type, s, nullptr);
+        if (rc != IPS4O_OK) return rc;
     }
-    if (!by_kernel) {
-        e = cudaMemcpyAsync(st->d_host_copy, h_ptr, bytes, cudaMemcpyHostToDevice, s);
-        if (e != cudaSuccess) { set_last_cuda_error(e, "cudaMemcpyAsync(H2D)"); return IPS4O_ERR_CUDA; }
-    }
-    rc = dispatch(*st, st->d_host_copy, n, key_type, s, nullptr);
-    if (rc != IPS4O_OK) return rc;
-    if (by_kernel) {
-        kernel_copy(h_dev, st->d_host_copy, bytes, s, st->sms, &e);
+    if (by_kernel && kernel_copy(h_dev, st->d_host_copy, bytes, s, st->sms, &e)) {
         if (e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (D2H)"); return IPS4O_ERR_CUDA; }
     } else {
         e = cudaMemcpyAsync(h_ptr, st->d_host_copy, bytes, cudaMemcpyDeviceToHost, s);

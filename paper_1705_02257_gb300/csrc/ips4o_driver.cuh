@@ -474,15 +474,18 @@ struct Driver {
         return i - i0;
     }
 
-    ips4o_status run_chunk(E* d, u32 nsub, u32 nstr, bool partition, u32* next_count) {
+    // src: where sampling and classification read the chunk's elements (d
+    // itself unless the sort starts from a copy elsewhere, see src0)
+    ips4o_status run_chunk(E* d, u32 nsub, u32 nstr, bool partition, u32* next_count, const E* src = nullptr) {
+        if (!src) src = d;
         IPS4O_CUDA(cudaMemcpyAsync(ws.subs, h_subs, nsub * sizeof(SubDesc), cudaMemcpyHostToDevice, stream));
         IPS4O_CUDA(cudaMemcpyAsync(ws.stripes, h_stripes, nstr * sizeof(StripeDesc), cudaMemcpyHostToDevice, stream));
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));
         const u64 seed = prm.seed;
-        IPS4O_LAUNCH(0, (k_sample<T, 512><<<nsub, 512, 0, stream>>>(d, ws, nsub, seed)));
+        IPS4O_LAUNCH(0, (k_sample<T, 512><<<nsub, 512, 0, stream>>>(src, ws, nsub, seed)));
         const int cgrid = (int)std::min<u32>(nstr, (u32)st.sms);
         IPS4O_LAUNCH(1, (k_classify<T><<<cgrid, ClassifyRegCfg<T>::TPB, ClassifyRegCfg<T>::smem_bytes, stream>>>(
-                            d, ws, nstr)));
+                            d, src, ws, nstr)));
         IPS4O_LAUNCH(2, (k_prefix<T, 256><<<nsub, 256, 0, stream>>>(ws, nsub)));
         IPS4O_LAUNCH(3, (k_fix<T, 256><<<st.sms * 2, 256, 0, stream>>>(d, ws)));
         IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
@@ -532,11 +535,21 @@ struct Driver {
         return IPS4O_OK;
     }
 
+    // The input of the first level when it is not d itself: a sort from a
+    // host buffer reads it there (through its device address) during the
+    // first sampling and classification, which write their blocks into d,
+    // so the copy to the device costs no pass of its own.
+    const E* src0 = nullptr;
+
     ips4o_status run(E* d, u64 n, PartitionOut* part) {
         ips4o_status rc = setup(n);
         if (rc != IPS4O_OK) return rc;
         st.stats.n = n;
-        if (!part && n <= (u64)rec_cap) return base_only(d, n);
+        if (!part && n <= (u64)rec_cap) {
+            if (src0 && src0 != d)
+                IPS4O_CUDA(cudaMemcpyAsync(d, src0, n * sizeof(E), cudaMemcpyDefault, stream));
+            return base_only(d, n);
+        }
         return levels(d, std::vector<Task>{Task{0, n}}, part);
     }
 
@@ -679,7 +692,7 @@ struct Driver {
                                           part != nullptr, &nsub, &nstr);
                 if (taken == 0) return IPS4O_ERR_INTERNAL;
                 u32 cnt = 0;
-                rc = run_chunk(d, nsub, nstr, part != nullptr, &cnt);
+                rc = run_chunk(d, nsub, nstr, part != nullptr, &cnt, level == 0 ? src0 : nullptr);
                 if (rc != IPS4O_OK) return rc;
                 for (u32 q = 0; q < nsub; ++q) st.stats.elements_distributed += h_subs[q].n;
                 if (cnt > 0) {
@@ -727,6 +740,15 @@ template <class T>
 ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
     Driver<T> drv(st, s);
     return drv.run((typename T::elem_t*)d, (u64)n, part);
+}
+
+// d[0, n) = the sorted elements of src[0, n) (src device-accessible, e.g. the
+// device address of pinned host memory; src is only read).
+template <class T>
+ips4o_status sort_from_t(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s) {
+    Driver<T> drv(st, s);
+    drv.src0 = (const typename T::elem_t*)src;
+    return drv.run((typename T::elem_t*)d, (u64)n, nullptr);
 }
 
 // Grow the stream's workspace and staging to what a call on n elements in

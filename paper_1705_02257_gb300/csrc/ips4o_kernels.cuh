@@ -409,8 +409,8 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
 // separate the splitters, else by the tree descent; the table is built once
 // per stripe from the subproblem's tree and gives the buckets of the descent.
 template <class T>
-__device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>& ws, u32 s,
-                                    unsigned char* smem_raw) {
+__device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::elem_t* src, const Workspace<T>& ws,
+                                    u32 s, unsigned char* smem_raw) {
     typedef ClassifyRegCfg<T> C;
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
@@ -448,6 +448,7 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
         }
         for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
         E* A = arr + sd.begin;
+        const E* S = src + sd.begin;                 // the stripe's input: A itself, or a copy elsewhere
         const u32 len = (u32)(sd.end - sd.begin);   // a stripe holds < 2^32 elements
         const u32 ntiles = (len + TILE - 1) / TILE;
         u32 front = 0;                       // full blocks written at the stripe front
@@ -507,7 +508,7 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 const u32 idx = tid + q * TPB;
-                if (tb + idx < len) nx[q] = A[tb + idx];
+                if (tb + idx < len) nx[q] = S[tb + idx];
             }
         };
         if (ntiles > 0) load_tile(0);
@@ -658,9 +659,12 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const Workspace<T>&
     }
 }
 
+// src: where the elements of the stripes are read (arr itself for the usual
+// in-place step; the first step of a sort from host memory reads the host
+// buffer through its device address and writes the blocks into arr).
 template <class T>
 __global__ void __launch_bounds__(ClassifyRegCfg<T>::TPB, 1)
-    k_classify(typename T::elem_t* arr, Workspace<T> ws, u32 nstripes) {
+    k_classify(typename T::elem_t* arr, const typename T::elem_t* src, Workspace<T> ws, u32 nstripes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ u32 s_stripe;
     for (;;) {
@@ -669,7 +673,7 @@ __global__ void __launch_bounds__(ClassifyRegCfg<T>::TPB, 1)
         const u32 s = s_stripe;
         __syncthreads();
         if (s >= nstripes) break;
-        classify_stripe_reg<T>(arr, ws, s, smem_raw);
+        classify_stripe_reg<T>(arr, src, ws, s, smem_raw);
     }
 }
 
