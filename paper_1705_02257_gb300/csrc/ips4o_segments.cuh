@@ -41,7 +41,7 @@ struct SegCfg {
     typedef typename T::key_t K;
     static constexpr int TPB = 1024;
     static constexpr int NW = TPB / 32;
-    static constexpr int NWP = 8;                       // mover warps of the block permutation
+    static constexpr int NWP = 128 / PermuteCfg<T>::V;  // mover warps of the block permutation (128 movers)
     static constexpr int B = T::kBlock;
     typedef BaseLarge<T> Base;
     static_assert(Base::TPB == TPB, "the base case runs on the whole CTA");
