@@ -889,7 +889,7 @@ struct PermuteCfg {
     static constexpr int TPB = 128;
     static constexpr int NW = TPB / 32;
     static constexpr int V = 8;                  // movers per warp (lanes 0..V-1)
-    static constexpr int MIN_CTAS = 6;           // per SM: 24 warps, 192 movers
+    static constexpr int MIN_CTAS = 6;           // register bound; shared memory admits 5 per SM (160 movers)
     static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block copy
     static constexpr int MAX_MOVERS_PER_BUCKET = 64;
     // block buffers of the warps, then one copy of the subproblem's tables
