@@ -147,12 +147,16 @@ typedef struct {
  * per recursion level; on return the sort has completed on the device. */
 ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream);
 
-/* Same as ips4o_sort but for an array in HOST memory: copies it to the
- * device, sorts, and copies the result back (all on `stream`).  The device
- * staging buffer is owned by the library and kept for reuse.  For pinned
- * host memory the copies are done by a kernel through the buffer's device
- * address (the GPU reads and writes pinned host memory directly), else by
- * cudaMemcpyAsync. */
+/* Same as ips4o_sort but for an array in HOST memory: the elements are
+ * brought to a device staging buffer (owned by the library and kept for
+ * reuse), sorted there, and copied back (all on `stream`); the call returns
+ * when h_ptr holds the result.  For pinned host memory the GPU reads and
+ * writes the buffer through its device address: for u64, f64 and pair keys
+ * the first distribution step samples and classifies the host buffer itself
+ * and writes its blocks into the staging buffer (no separate copy to the
+ * device), and a kernel copies the result back; inputs no larger than the
+ * base case and 100-byte records are copied by a kernel first.  Pageable
+ * memory is copied by cudaMemcpyAsync. */
 ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream);
 
 /* One distribution step (Section 4: sampling, local classification, block

@@ -6,10 +6,11 @@
 //                on equality buckets when there were any (Sections 4.4, 4.7),
 //                build the implicit search tree.
 //   k_classify   Section 4.1 "Local Classification": every stripe is streamed
-//                through shared memory, each element is classified with the
-//                tree and appended to its bucket's buffer block; a full buffer
-//                block is written back over the front of the stripe.  Counts
-//                per bucket and the partially filled buffers are kept.
+//                through registers in 64 KiB tiles, each element is classified
+//                (through the splitter lookup table, or the tree descent) and
+//                appended to its bucket's buffer block in shared memory; a full
+//                buffer block is written back over the front of the stripe.
+//                Counts per bucket and the partially filled buffers are kept.
 //   k_prefix     Section 4.2: prefix sums give the bucket boundaries, the
 //                delimiters d_i (rounded up to blocks) and the initial write
 //                and read pointers w_i, r_i; buckets crossing a stripe boundary
@@ -17,10 +18,11 @@
 //   k_fix        Appendix A "Empty block movement": within each bucket region,
 //                full blocks from the back fill the empty blocks at the front,
 //                so every region reads "full blocks, then empty blocks".
-//   k_permute    Section 4.2 "Block Permutation": persistent movers (one warp
-//                each, the GPU counterpart of a thread with two swap buffers)
-//                with primary buckets, atomic (w_i, r_i) updates in one 64-bit
-//                word, reader counts, and the skip of blocks already in place.
+//   k_permute    Section 4.2 "Block Permutation": persistent movers (lanes of
+//                a warp, each the GPU counterpart of a thread with two swap
+//                buffers) with primary buckets, atomic (w_i, r_i) updates in one
+//                64-bit word, reader counts, and the skip of blocks already in
+//                place.
 //   k_cleanup    Section 4.3 "Cleanup": per bucket, the overshoot of its last
 //                block, the partial buffers of all stripes and the overflow
 //                block are written into the empty head and tail of the bucket;
