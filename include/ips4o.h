@@ -86,7 +86,7 @@ typedef struct {
     int base_case_max;    /* buckets of at most this many elements are sorted in shared memory
                              (clamped to [16, ips4o_base_case_capacity]); smaller values force
                              deeper recursion; <= 0 selects the capacity */
-    int stripes_per_sm;   /* stripes (local-classification work items) per SM for a level; default 2 */
+    int stripes_per_sm;   /* fewest stripes (local-classification work items) per SM tried for a level; default 1 */
     int profile;          /* 1: time every kernel with CUDA events into ips4o_stats.phase_ms */
     uint64_t seed;        /* sampling seed */
     int segment_scheduler;  /* ips4o_sort_segmented / ips4o_sort_batched: 0 automatic (currently

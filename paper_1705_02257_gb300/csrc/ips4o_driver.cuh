@@ -383,7 +383,7 @@ struct Driver {
     // stripes dynamically, so the number of stripes should fill whole waves
     // of SMs.  Stripes of a subproblem have equal length and never cross it,
     // so with many subproblems the count is a sum of per-subproblem
-    // roundings: try 2, 3, ... stripes per SM (from the stripes_per_sm
+    // roundings: try 1, 2, ... stripes per SM (from the stripes_per_sm
     // parameter on) and keep the count whose last wave is fullest, with a
     // small charge for extra stripes (more partial buffers to clean up).
     u64 pick_stripe_len(const Task* tasks, size_t count, u64 level_total) const {
