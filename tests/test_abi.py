@@ -45,6 +45,11 @@ def test_argument_errors_without_device_work(lib):
     assert ips4o.ips4o_sort(8 * 1024 + 2, 10, ips4o.REC100_K10, 0) == 3   # records: 4-byte alignment
     assert ips4o.ips4o_sort(0, 0, ips4o.U64, 0) == 0            # empty input: no-op
     assert ips4o.ips4o_sort(0, 1, ips4o.U64, 0) == 0
+    # more than 16 GiB of elements in one call (the packed pointer word's
+    # region limit): refused before any device work
+    assert ips4o.ips4o_sort(8 * 1024, (16 << 30) // 8 + 1, ips4o.U64, 0) == 8
+    assert ips4o.ips4o_sort(16 * 1024, (16 << 30) // 16 + 1, ips4o.PAIR_U64, 0) == 8
+    assert ips4o.ips4o_sort_host(8 * 1024, (16 << 30) // 8 + 1, ips4o.U64, 0) == 8
     assert ips4o.ips4o_status_string(6) == "bounded device wait timed out"
 
 
