@@ -28,8 +28,7 @@
  *     side by side on the device, each with its own workspace.  Calls are not
  *     capturable in a CUDA graph: the host driver reads the number of
  *     subproblems of each recursion level back from the device before it
- *     launches the next level (ips4o_sort_noalloc is the exception for the
- *     allocation part only).
+ *     launches the next level (ips4o_sort_segmented_async is the exception).
  *   - Return codes: argument errors are detected before any work is queued;
  *     device-side errors (an exhausted bounded wait, a broken internal
  *     invariant) are reported by the call that detects them through the
@@ -232,22 +231,32 @@ ips4o_status ips4o_stream_status(void* stream);
 
 /* Sort d_ptr[0..n) in place, like ips4o_sort, without allocating any memory.
  * The paper has no counterpart: this entry point serves callers that cannot
- * allocate when they sort (for example while a stream is being captured into
- * a CUDA graph, or a service whose device memory is fixed at start-up).
+ * allocate device memory when they sort, such as a service whose device
+ * footprint is fixed at start-up (a later allocation could fail or push out
+ * other tenants) or a plug-in whose host process owns every allocation.
  * Instead of the workspace it uses a scratch area built into the library: a
  * 16 MiB __device__ array, which every GPU that loads the library holds until
- * the process exits, plus a static host staging buffer.
+ * the process exits, plus a static host staging buffer.  It calls no
+ * cudaMalloc, cudaMallocHost, cudaFree or other allocating routine.
  *   - n is limited to 2^20 elements; larger n returns IPS4O_ERR_TOO_LARGE
  *     before any work is queued.  The library's default parameters are used
  *     (ips4o_set_params does not apply), and ips4o_get_stats does not report
  *     these calls.
+ *   - The call synchronises `stream` once per recursion level, so it cannot
+ *     be made while the stream is being captured into a CUDA graph: it then
+ *     returns IPS4O_ERR_INVALID_ARG before queuing anything (the capture
+ *     stays valid).  Work that must be captured can use
+ *     ips4o_sort_segmented_async with a reserved workspace.
  *   - The first call on a device looks up the device address of the scratch
- *     array (cudaGetSymbolAddress); make that first call before any stream
- *     capture.
- *   - All calls share the scratch array and keep the last call's contents;
- *     calls are serialised by the library and each waits for its own work, so
- *     calls must not overlap on the GPU (they would race on the scratch).
- *   - Same argument checks and return codes as ips4o_sort. */
+ *     array (cudaGetSymbolAddress) with that device current.
+ *   - All calls share the scratch array and keep the last call's contents
+ *     (counters that must start at zero are cleared by every call); calls are
+ *     serialised by the library and each waits for its own work, since calls
+ *     that overlapped on the GPU would race on the scratch.
+ *   - Same argument checks and return codes as ips4o_sort.  As there, an
+ *     error reported after the first level has run (a bounded wait that gave
+ *     up, a failed invariant check) leaves d_ptr holding the same elements,
+ *     permuted but not sorted. */
 ips4o_status ips4o_sort_noalloc(void* d_ptr, size_t n, int key_type, void* stream);
 
 /* Device workspace the library needs for a sort of n elements of the type. */

@@ -66,7 +66,7 @@ std::mutex g_mtx;
 // different streams run side by side, calls on one stream are serialised
 std::map<std::pair<int, uintptr_t>, DeviceState*> g_states;
 ips4o_stats g_last_stats[64];
-ips4o_params g_params = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0};
+ips4o_params g_params = kDefaultParams;
 thread_local char g_last_err[256] = {0};
 ips4o_class_params g_classes[IPS4O_NUM_CLASSES] = {};
 }  // namespace
@@ -439,7 +439,7 @@ ips4o_status ips4o_release_workspace(void) {
 ips4o_status ips4o_set_params(const ips4o_params* p) {
     std::lock_guard<std::mutex> lk(g_mtx);
     if (!p) {
-        g_params = ips4o_params{256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0};
+        g_params = kDefaultParams;
         return IPS4O_OK;
     }
     if (p->k_max < 4 || p->k_max > 256 || (p->k_max & (p->k_max - 1)) != 0) return IPS4O_ERR_INVALID_ARG;

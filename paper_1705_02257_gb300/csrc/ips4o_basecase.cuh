@@ -1,14 +1,18 @@
 // ips4o_basecase.cuh — splitter selection (Sections 3, 4.4, 4.7) and the
-// shared-memory base case.
+// shared-memory base case (Section 4.7).
 //
-// The base case sorts one bucket of at most T elements with one CTA.  It is
-// the method's own recursion carried out on chip: the bucket is loaded once
-// into registers and shared memory, a sample gives up to 255 splitters
-// (equality buckets when the sample repeats keys), every element is
-// classified with the implicit search tree and scattered into its
-// sub-bucket in shared memory, and the sub-buckets, about n0 = 16 elements
-// each (Section 4.7), are finished by insertion sort.  The bucket is read
-// from and written to global memory exactly once.
+// The base case sorts one bucket of at most CAP elements with one CTA, in
+// place of the paper's insertion sort of at most n0 = 16 elements.  The
+// bucket is read once into registers; its key range is split into about one
+// sub-range of equal power-of-two width per element (a bucket left by the
+// sampled distribution steps is close to uniform over its range), the
+// elements are counted and scattered into their sub-ranges in shared memory,
+// and each element is written to global memory at its sub-range's start plus
+// its rank among the keys of that sub-range.  Sub-ranges of more than LIMIT
+// elements (clustered or repeated keys) are sorted afterwards, one at a time
+// by the whole CTA, with a bitonic network in shared memory (or left as they
+// are when all their keys are equal).  The bucket is read from and written
+// to global memory once.
 #pragma once
 
 #include "ips4o_common.cuh"

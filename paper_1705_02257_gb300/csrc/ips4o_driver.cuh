@@ -227,7 +227,14 @@ struct Driver {
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
     Driver(DeviceState& s, cudaStream_t strm, const ips4o_params& p) : st(s), stream(strm), prm(p) {}
 
-    ips4o_status setup(u64 n, u64 init_cap = 0, const Caps<T>* override_caps = nullptr, bool may_allocate = true) {
+    // How setup treats the buffers of the stream state:
+    //   kGrow     grow the workspace and host staging as needed (may allocate);
+    //   kEnqueue  use the reserved workspace, no host staging (enqueue-only calls);
+    //   kFixed    use the given workspace and host staging as they are: never
+    //             allocates or frees, TOO_LARGE when either is too small.
+    enum WsMode { kGrow, kEnqueue, kFixed };
+
+    ips4o_status setup(u64 n, u64 init_cap = 0, const Caps<T>* override_caps = nullptr, WsMode mode = kGrow) {
         cudaGetLastError();   // an error left by an earlier, unrelated runtime call is not this call's
         st.d_status = nullptr;  // the workspace layout changes: an earlier status word is gone
         if (override_caps) {
@@ -238,12 +245,13 @@ struct Driver {
         }
         const size_t need = carve<T>(caps, nullptr, nullptr);
         ips4o_status rc = IPS4O_OK;
-        if (may_allocate) rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
+        if (mode == kGrow) rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
         else if (!st.d_ws || st.ws_bytes < need) rc = IPS4O_ERR_TOO_LARGE;
         if (rc != IPS4O_OK) return rc;
+        if (mode == kFixed && (!st.h_stage || st.h_stage_bytes < host_stage_bytes<T>(caps))) return IPS4O_ERR_TOO_LARGE;
         carve<T>(caps, (char*)st.d_ws, &ws);
-        if (may_allocate) {
-            rc = ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(caps));
+        if (mode != kEnqueue) {
+            if (mode == kGrow) rc = ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(caps));
             if (rc != IPS4O_OK) return rc;
             char* h = (char*)st.h_stage;
             h_subs = (SubDesc*)h;
@@ -660,7 +668,7 @@ struct Driver {
     // status word that ips4o_stream_status reads.
     ips4o_status enqueue_scheduler(E* d, const u64* d_off, u64 num_segments) {
         const Caps<T> c = caps_for_scheduler<T>(st.sms, num_segments);
-        ips4o_status rc = setup(0, 0, &c, false);
+        ips4o_status rc = setup(0, 0, &c, kEnqueue);
         if (rc != IPS4O_OK) return rc;
         st.d_status = &ws.ctr->status;
         IPS4O_CUDA(cudaMemsetAsync(ws.ctr, 0, sizeof(ChunkCounters), stream));

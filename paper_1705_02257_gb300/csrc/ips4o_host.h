@@ -30,6 +30,9 @@ struct DeviceState {
     ips4o_stats stats{};
 };
 
+// The library's default parameters (what ips4o_set_params(NULL) restores).
+constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0};
+
 DeviceState* stream_state(void* stream, cudaError_t* err);   // state of (current device, stream)
 DeviceState* current_device_state(cudaError_t* err);          // state of (current device, NULL stream)
 ips4o_params& global_params();
@@ -67,8 +70,12 @@ ips4o_status upload_class_table_u64(const ips4o_class_params* t);
 ips4o_status upload_class_table_f64(const ips4o_class_params* t);
 ips4o_status upload_class_table_pair(const ips4o_class_params* t);
 
-// ips4o_sort_noalloc's level loop; tasks = 2 * kNoAllocMaxTasks entries
-constexpr size_t kNoAllocMaxTasks = 256;   // subproblems per level (n / 16Ki << 256)
+// ips4o_sort_noalloc: its fixed scratch and limits, and its level loop
+// (tasks = 2 * kNoAllocMaxTasks entries)
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // device scratch, 16 MiB
+constexpr size_t kNoAllocHostBytes = (size_t)1 << 20;       // host staging, 1 MiB
+constexpr size_t kNoAllocMaxN = (size_t)1 << 20;            // largest array, in elements
+constexpr size_t kNoAllocMaxTasks = 256;                    // subproblems per level
 ips4o_status sort_noalloc_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
 ips4o_status sort_noalloc_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);
 ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, Task* tasks);

@@ -1,16 +1,21 @@
 // ips4o_noalloc.cu — ips4o_sort_noalloc: the sort for callers that must not
 // allocate memory.
 //
-// Some callers cannot call cudaMalloc at the time they sort: code running
-// while a stream is being captured into a CUDA graph (allocation is not
-// allowed there), memory-budgeted services that must not grow the device
-// footprint after start-up, or plug-ins whose host process owns all device
-// allocations.  For them this entry point sorts arrays of up to
-// kNoAllocMaxN elements using a fixed scratch area that is part of the
-// library image: a file-scope __device__ array (kNoAllocScratchBytes, held on
-// every GPU that loads the library until the process exits) and a static
-// host staging buffer.  It calls no cudaMalloc, cudaMallocHost, cudaFree or
-// other allocating routine.
+// Some callers cannot call cudaMalloc when they sort: memory-budgeted
+// services whose device footprint is fixed at start-up (a later allocation
+// could fail or push out other tenants), or plug-ins whose host process owns
+// every device allocation.  For them this entry point sorts arrays of up to
+// kNoAllocMaxN elements in a fixed scratch area that is part of the library
+// image: a file-scope __device__ array (kNoAllocScratchBytes, held on every
+// GPU that loads the library until the process exits) and a static host
+// staging buffer.  It calls no cudaMalloc, cudaMallocHost, cudaFree or other
+// allocating routine; a sort whose workspace would not fit the scratch is
+// refused with IPS4O_ERR_TOO_LARGE before any work is queued.
+//
+// The call still synchronises its stream once per recursion level (the
+// next level is planned on the host), so it cannot run while the stream is
+// being captured into a CUDA graph: it checks that first and returns
+// IPS4O_ERR_INVALID_ARG without touching the stream.
 //
 // The scratch array is shared by every call: calls that overlap on the GPU
 // (different streams, or different host threads) would race on it, so the
@@ -24,10 +29,6 @@
 #include "ips4o_host.h"
 
 namespace ips4o {
-
-constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;   // device scratch, 16 MiB
-constexpr size_t kNoAllocHostBytes = (size_t)1 << 20;       // host staging, 1 MiB
-constexpr size_t kNoAllocMaxN = (size_t)1 << 20;            // largest array, in elements
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 alignas(256) static unsigned char g_noalloc_host[kNoAllocHostBytes];
@@ -54,8 +55,17 @@ extern "C" ips4o_status ips4o_sort_noalloc(void* d_ptr, size_t n, int key_type, 
     if (n > 1 && !d_ptr) return IPS4O_ERR_INVALID_ARG;
     if (d_ptr && ((uintptr_t)d_ptr % es) != 0) return IPS4O_ERR_MISALIGNED;
     if (n < 2) return IPS4O_OK;
+    // the level loop synchronises the stream: refuse a stream under capture
+    // before anything is queued on it (the capture stays valid)
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        if (e != cudaSuccess) cudaGetLastError();
+        set_last_message("ips4o_sort_noalloc: the stream is being captured; the call synchronises per level");
+        return IPS4O_ERR_INVALID_ARG;
+    }
     int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     if (dev < 0 || dev >= 64) return IPS4O_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_noalloc_mtx);

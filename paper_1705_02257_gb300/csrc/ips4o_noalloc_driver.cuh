@@ -9,9 +9,16 @@
 
 namespace ips4o {
 
-// The library defaults: the scratch is sized for them, so user parameters
-// (e.g. a smaller base case, which creates more subproblems) do not apply.
-static const ips4o_params kNoAllocParams = {256, 0, 0, 2, 0, 0x2545F4914F6CDD1Dull};
+// The library defaults (ips4o_set_params(NULL)): the scratch is sized for
+// them, so user parameters (e.g. a smaller base case, which creates more
+// subproblems) do not apply.
+static const ips4o_params kNoAllocParams = kDefaultParams;
+
+// Every next-level subproblem is larger than the recursion threshold, so a
+// level of an array of at most kNoAllocMaxN elements has fewer than
+// kNoAllocMaxN / (threshold + 1) of them; with the default parameters the
+// smallest threshold is the pair base case.
+static_assert(kNoAllocMaxN / ((size_t)TPair::kBaseCap + 1) < kNoAllocMaxTasks, "task arrays too small");
 
 template <class T>
 struct NoAllocDriver : Driver<T> {
@@ -29,12 +36,10 @@ struct NoAllocDriver : Driver<T> {
     NoAllocDriver(DeviceState& s, cudaStream_t strm, Task* t) : Driver<T>(s, strm, kNoAllocParams), tasks(t) {}
 
     ips4o_status run(E* d, u64 n) {
-        // the scratch must hold this sort's workspace: refuse rather than
-        // letting the workspace helpers replace it with an allocation
-        const Caps<T> c = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
-        if (carve<T>(c, nullptr, nullptr) > st.ws_bytes || host_stage_bytes<T>(c) > st.h_stage_bytes)
-            return IPS4O_ERR_TOO_LARGE;
-        ips4o_status rc = this->setup(n);
+        // the scratch is used as it is: setup never allocates or frees in
+        // this mode and answers TOO_LARGE when the workspace or the host
+        // staging this sort needs does not fit
+        ips4o_status rc = this->setup(n, 0, nullptr, Driver<T>::kFixed);
         if (rc != IPS4O_OK) return rc;
         st.stats.n = n;
         if (n <= (u64)rec_cap) return this->base_only(d, n);

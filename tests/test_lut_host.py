@@ -35,3 +35,20 @@ def test_lookup_table_equals_brute_force_count(tmp_path):
     r = subprocess.run([exe, "600"], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout + r.stderr
     assert int(r.stdout.split()[1]) > 1_000_000
+
+
+def test_noalloc_scratch_holds_every_accepted_sort(tmp_path):
+    """ips4o_sort_noalloc refuses sizes above 2^20 elements; below that its
+    fixed 16 MiB device scratch and 1 MiB host staging must hold the
+    workspace the driver's sizing rules ask for, for every element type and
+    any SM count up to 160 (tests/host/noalloc_fit.cu, host only)."""
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "noalloc_fit")
+    cmd = [nvcc, "-std=c++17", "-O1", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC,
+           os.path.join(HERE, "host", "noalloc_fit.cu"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout + r.stderr

@@ -223,3 +223,28 @@ def test_rec100_key_is_big_endian_bytes():
     k = oracle.keys(r, "rec100")[0]
     assert int(k[0]) == int.from_bytes(bytes(range(1, 9)), "big")
     assert int(k[1]) == (9 << 8) | 10
+
+
+def test_splitters_are_equally_spaced_order_statistics():
+    # Section 3: the k-1 splitters are picked equidistantly from the sorted
+    # sample of alpha*k - 1 keys, s_j = sample[j*alpha - 1], i.e. s_j is the
+    # (j*alpha)-th smallest of the sample.  For a sample drawn uniformly from
+    # the keys 0..n-1, the r-th smallest of m draws has mean about
+    # r / (m + 1) * n (order statistics of the uniform distribution), so with
+    # k = 8, alpha = 3 (m = 23) the mean of s_j / n is j / 8.  Taking the
+    # neighbouring sample entry instead (j*alpha or j*alpha - 2) shifts every
+    # mean by 1/24, far outside the tolerance over 400 seeded samples.
+    n = 1 << 16
+    a = np.random.default_rng(5).permutation(n).astype(np.uint64)
+    k, alpha = 8, 3
+    rows = []
+    for seed in range(1, 401):
+        _, spl, eq, _ = oracle.partition(a, "u64", k=k, alpha=alpha, adaptive=False, seed=seed)
+        if eq or len(spl) != k - 1:
+            continue                      # the sample repeated a key (rare with distinct keys)
+        rows.append(spl[:, 0].astype(np.float64) / n)
+    assert len(rows) >= 390
+    means = np.mean(np.array(rows), axis=0)
+    expected = np.arange(1, k) / k
+    assert np.all(np.abs(means - expected) < 0.025), means
+    assert abs(float(np.mean(means - expected))) < 0.012, means

@@ -38,6 +38,9 @@ MUTANTS = {
     # record key bytes 8 and 9 swapped
     "rec100_lo": ("k.lo = ((uint64_t)e[8] << 8) | e[9];",
                   "k.lo = ((uint64_t)e[9] << 8) | e[8];"),
+    # splitters taken one place off the equal spacing of Section 3
+    "splitter_spacing": ("okey c = sample[(size_t)j * alpha - 1];",
+                         "okey c = sample[(size_t)j * alpha - (j < k - 1 ? 0 : 1)];"),
     # range buckets skipped instead of equality buckets during recursion
     "recurse_skip": ("if (L.eq && (b % 2 == 1)) continue;",
                      "if (L.eq && (b % 2 == 0)) continue;"),
