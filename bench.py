@@ -152,6 +152,32 @@ class ClockSampler:
         return out
 
 
+def _transfer_bound(h_buf, d_buf, stream, reps: int) -> dict:
+    """Copy-engine time of one host -> device and one device -> host copy of
+    the step's bytes between pinned host memory and HBM: the least an end-to-
+    end sort that must bring its input in and its result back can take when
+    the two transfers do not overlap each other."""
+    import torch
+    d_tmp = torch.empty_like(d_buf)
+    h_tmp = torch.empty_like(h_buf).pin_memory()
+    res = {}
+    for name, dst, src in (("h2d", d_tmp, h_buf), ("d2h", h_tmp, d_buf)):
+        dst.copy_(src, non_blocking=True)                      # warm-up
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        for _ in range(reps):
+            dst.copy_(src, non_blocking=True)
+        e.record(stream)
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        res[f"{name}_ms"] = ms
+        res[f"{name}_gbs"] = src.numel() / (ms * 1e-3) / 1e9
+    res["transfer_bound_ms"] = res["h2d_ms"] + res["d2h_ms"]
+    del d_tmp, h_tmp
+    return res
+
+
 def cpu_baseline(log2n_sample: int = 24, reps: int = 1, kt: str = "u64", dist: str = "uniform"):
     """The oracle, as it stands, single-threaded on a bounded sample."""
     import oracle
@@ -342,6 +368,11 @@ def run_gpu(args):
         e2e = {"value": n * world * args.steps / e2e_total, "unit": METRIC,
                "h2d_bytes_per_step": n * elem, "d2h_bytes_per_step": n * elem,
                "ms_per_step": 1e3 * e2e_total / args.steps, "host_memory": "pinned"}
+        # the transfer bound: the same bytes copied host -> device and back
+        # by the copy engines (pinned buffers, CUDA events), no sort between
+        e2e.update(_transfer_bound(h_in, pristine, stream, max(1, min(5, args.steps))))
+        e2e["frac_of_transfer_bound"] = e2e["transfer_bound_ms"] / e2e["ms_per_step"]
+        del h_in, h_work
 
     if rank != 0:
         if dist_on:
