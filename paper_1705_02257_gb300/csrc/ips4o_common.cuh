@@ -31,7 +31,9 @@ constexpr unsigned long long kClaimRead = 1ull - (1ull << kRdBits);   // readers
 constexpr unsigned long long kClaimWrite = 1ull << kWShift;          // w + 1
 constexpr unsigned long long kReadDone = ~0ull;                      // readers - 1
 constexpr unsigned long long kMaxRegionBlocks = (1ull << kRBits) - kRBias - 2;
-constexpr unsigned kMaxMoversPerSub = 16000;              // < 2^kRdBits concurrent readers
+// Reader counts are held per warp (the read claims of a warp's movers on one
+// bucket are combined), so a subproblem may have this many mover warps.
+constexpr unsigned kMaxReadersPerSub = 16000;             // < 2^kRdBits concurrent readers
 
 // Device status word bits.
 constexpr u32 kStatusTimeout = 1u;     // a bounded wait gave up
@@ -363,6 +365,38 @@ __host__ __device__ __forceinline__ bool lut_cell_start_log(u32 c, u64 base, u64
     }
     if (off > ~base) return false;
     *start = base + off;
+    return true;
+}
+
+// Linear cells aligned to multiples of 2^shift of the key domain: cell
+// c(e) = (e >> shift) - c0 with c0 = s_1 >> shift, clamped to
+// [0, kLutCells - 1], so cell 0 also takes every key below its range and the
+// last cell is open upwards.  lut_abs_shift picks shift such that s_1 and
+// s_{L-1} are at most kLutCells - 1 cells apart.  For shift >= 32 the cell
+// follows from the key's high 32 bits alone (lut_cell_abs_hi).
+__host__ __device__ __forceinline__ u32 lut_abs_shift(u64 base, u64 top) {
+    u32 sh = lut_shift(base, top);
+    if ((top >> sh) - (base >> sh) >= (u64)kLutCells) ++sh;
+    return sh;
+}
+__host__ __device__ __forceinline__ u32 lut_cell_abs(u64 e, u64 c0, u32 shift) {
+    const u64 h = e >> shift;
+    const u64 d = h - c0;
+    return h < c0 ? 0u : (d < (u64)(kLutCells - 1) ? (u32)d : (u32)(kLutCells - 1));
+}
+__host__ __device__ __forceinline__ u32 lut_cell_abs_hi(u32 ehi, u32 c0, u32 shift_hi) {
+    const u32 h = ehi >> shift_hi;
+    const u32 d = h - c0;
+    return h < c0 ? 0u : (d < (u32)(kLutCells - 1) ? d : (u32)(kLutCells - 1));
+}
+// First key of cell c (0 for cell 0, which holds every key below cell 1);
+// false when it lies above the key domain (no key maps to the cell).
+__host__ __device__ __forceinline__ bool lut_cell_start_abs(u32 c, u64 c0, u32 shift, u64* start) {
+    if (c == 0) { *start = 0; return true; }
+    const u64 h = c0 + c;
+    if (h < c0) return false;
+    if (shift > 0 && (h >> (64 - shift)) != 0) return false;
+    *start = h << shift;
     return true;
 }
 

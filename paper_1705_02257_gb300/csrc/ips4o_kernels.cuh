@@ -123,28 +123,32 @@ struct ClassifyRegCfg {
     static constexpr int TILE = 65536 / (int)sizeof(E);        // 64 KiB per tile
     static constexpr int IPT = TILE / TPB;
     static constexpr int B = T::kBlock;
-    static constexpr int MAXBLK = 384;                        // >= (256*(B-1) + TILE) / B
+    static constexpr int CH = 16 / (int)sizeof(E);             // elements per 16-byte chunk (one per lane and block)
+    // grouping area: the new elements of the buckets that emit blocks in a
+    // tile, each bucket's run starting at a parity that makes its blocks
+    // 16-byte aligned (at most one element of padding per bucket and end)
+    static constexpr int GRP = TILE + 2 * kMaxBuckets;
+    static constexpr int MAXBLK = 384;                         // >= (256*(B-1) + TILE) / B
     static constexpr size_t off_buf = 0;
     static constexpr size_t off_grp = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
-    static constexpr size_t off_tree = off_grp + (size_t)TILE * sizeof(E);
+    static constexpr size_t off_tree = off_grp + (size_t)GRP * sizeof(E);
     static constexpr size_t off_spl = off_tree + kMaxLeaves * sizeof(K);
-    static constexpr size_t off_fill = off_spl + kMaxLeaves * sizeof(K);
-    static constexpr size_t off_cnt = off_fill + kMaxBuckets * 4;
-    static constexpr size_t off_off = off_cnt + kMaxBuckets * 4;
-    static constexpr size_t off_bscan = off_off + kMaxBuckets * 4;
-    static constexpr size_t off_total = off_bscan + kMaxBuckets * 4;
-    static constexpr size_t off_blkb = off_total + kMaxBuckets * 4;
-    static constexpr size_t off_emit = off_blkb + MAXBLK * 2;
-    static constexpr size_t off_misc = off_emit + kMaxBuckets * 2;
-    static constexpr size_t off_lut = off_misc + 64 * 8;    // u16[kLutCells + 1]: lo | hi << 8
-    static constexpr size_t off_dst = off_lut + (kLutCells + 8) * 2;   // u32[kMaxBuckets]
-    static constexpr size_t smem_bytes = off_dst + kMaxBuckets * 4;
-    static_assert(off_grp % sizeof(E) == 0 && off_buf == 0, "destinations count elements from the base");
+    static constexpr size_t off_fill = off_spl + (kMaxLeaves + 8) * sizeof(K);
+    static constexpr size_t off_cnt = off_fill + kMaxBuckets * 4;          // u32[2][kMaxBuckets]
+    static constexpr size_t off_total = off_cnt + 2 * kMaxBuckets * 4;
+    static constexpr size_t off_dst = off_total + kMaxBuckets * 4;
+    static constexpr size_t off_binfo = off_dst + kMaxBuckets * 4;         // uint2[2][kMaxBuckets]
+    static constexpr size_t off_desc = off_binfo + 2 * kMaxBuckets * 8;    // u32[2][MAXBLK]
+    static constexpr size_t off_misc = off_desc + 2 * MAXBLK * 4;         // u32[16]
+    static constexpr size_t off_lut = off_misc + 64;                       // u16[kLutCells + 8]
+    static constexpr size_t smem_bytes = off_lut + (kLutCells + 8) * 2;
+    static_assert(off_grp % 16 == 0 && off_buf == 0, "destinations count elements from the base");
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
-    static_assert(MAXBLK < 65536 && TILE < (1 << 30), "packed scan fields");
     static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
-    static_assert(kLutCells % TPB == 0 && (size_t)TILE * sizeof(E) >= kLutCells, "table build layout");
-    static_assert(TILE <= 65536, "ranks are packed in 16 bits");
+    static_assert(kLutCells % TPB == 0 && (size_t)GRP * sizeof(E) >= kLutCells, "table build layout");
+    static_assert(TILE <= 65536 && GRP + 64 < 65536, "ranks and grouping offsets are packed in 16 bits");
+    static_assert(B * (int)sizeof(E) == 32 * 16 && CH >= 1, "a block is one 16-byte chunk per lane");
+    static_assert(smem_bytes <= 232448, "shared memory of one CTA");
 };
 
 // Bucket ids of IPT keys, descending the tree level by level for all keys at
@@ -401,264 +405,344 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
     }
 }
 
-// The same local classification with larger tiles held in registers
-// (ClassifyRegCfg<T>::TPB threads): each thread keeps IPT elements of the
-// current tile and loads its elements of the next tile while the current one
-// is classified and distributed, so shared memory needs no input staging
-// and holds one grouping area for the elements of buckets that emit blocks.
-// Twice the elements per tile halve the barriers per element.  Keys are
-// classified through the splitter lookup table (lut_refine) where its cells
-// separate the splitters, else by the tree descent; the table is built once
-// per stripe from the subproblem's tree and gives the buckets of the descent.
+// Local classification of stripe s (Section 4.1) with tiles held in
+// registers (ClassifyRegCfg<T>::TPB threads).  Each thread keeps IPT
+// elements of the current tile and loads its elements of the next tile while
+// the current one is processed, so shared memory holds no input staging.
+// Keys are classified through the splitter lookup table (lut_refine) where
+// its cells separate the splitters, else by the tree descent; the table is
+// built once per stripe from the subproblem's tree and gives the buckets of
+// the descent.
+//
+// A tile goes through three phases separated by barriers:
+//   A  warp 0 turns the tile's bucket counts into destinations (the bucket's
+//      buffer block, or for a bucket whose buffer fills, a run in the
+//      grouping area that starts at the parity which makes its blocks 16-byte
+//      aligned), block descriptors and new fill levels; meanwhile the other
+//      warps write the full blocks of the previous tile over the front of the
+//      stripe, one 16-byte chunk per lane, and copy each emitting bucket's
+//      remainder back into its buffer block;
+//   B  every thread scatters its elements to their destinations;
+//   C  every thread classifies its elements of the next tile and takes their
+//      ranks within their buckets (shared-memory counters, double-buffered
+//      so that phase A of this tile may still read the other set).
 template <class T>
 __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::elem_t* src, const Workspace<T>& ws,
                                     u32 s, unsigned char* smem_raw) {
     typedef ClassifyRegCfg<T> C;
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    constexpr int TPB = C::TPB, NW = C::NW, TILE = C::TILE, IPT = C::IPT, B = C::B;
+    constexpr int TPB = C::TPB, NW = C::NW, TILE = C::TILE, IPT = C::IPT, B = C::B, CH = C::CH;
+    constexpr u32 GRP0 = (u32)(C::off_grp / sizeof(E));   // grouping area, in elements from the base
     E* buf = (E*)(smem_raw + C::off_buf);
-    E* grp = (E*)(smem_raw + C::off_grp);          // grouping area of the emitting buckets
+    E* grp = (E*)(smem_raw + C::off_grp);
     K* s_tree = (K*)(smem_raw + C::off_tree);
     K* s_spl = (K*)(smem_raw + C::off_spl);
     u32* s_fill = (u32*)(smem_raw + C::off_fill);
     u32* s_cnt = (u32*)(smem_raw + C::off_cnt);
-    u32* s_off = (u32*)(smem_raw + C::off_off);     // grouped-tile offset of a bucket that fills a block
-    u32* s_bscan = (u32*)(smem_raw + C::off_bscan);
     u32* s_total = (u32*)(smem_raw + C::off_total);
-    unsigned short* s_blkb = (unsigned short*)(smem_raw + C::off_blkb);
-    unsigned short* s_emit = (unsigned short*)(smem_raw + C::off_emit);   // buckets emitting in this tile
-    u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0..32) scan tmp
-    unsigned short* s_lut = (unsigned short*)(smem_raw + C::off_lut);
     // where the tile's next element of a bucket goes, in elements from the
-    // start of shared memory: its buffer block, or its grouping-area slot
+    // start of shared memory: its buffer block, or its grouping-area run
     u32* s_dst = (u32*)(smem_raw + C::off_dst);
+    uint2* s_binfo = (uint2*)(smem_raw + C::off_binfo);
+    u32* s_desc = (u32*)(smem_raw + C::off_desc);
+    u32* s_misc = (u32*)(smem_raw + C::off_misc);   // [0..1] blocks of a tile, [2..3] stripe front before it
+    unsigned short* s_lut = (unsigned short*)(smem_raw + C::off_lut);
     E* s_elem = (E*)smem_raw;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    {
-        const StripeDesc sd = ws.stripes[s];
-        const SubDesc sub = ws.subs[sd.sub];
-        const int logL = (int)sub.log_leaves;
-        const bool eq = sub.eq != 0;
-        u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
-        u32* s_tlo = s_thi + kMaxLeaves;
-        for (int i = tid; i < kMaxLeaves; i += TPB) {
-            const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
-            s_thi[i] = (u32)(a >> 32);
-            s_tlo[i] = (u32)a;
-            s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
-        }
-        for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
-        E* A = arr + sd.begin;
-        const E* S = src + sd.begin;                 // the stripe's input: A itself, or a copy elsewhere
-        const u32 len = (u32)(sd.end - sd.begin);   // a stripe holds < 2^32 elements
-        const u32 ntiles = (len + TILE - 1) / TILE;
-        u32 front = 0;                       // full blocks written at the stripe front
-        __syncthreads();
-        // The splitter lookup table.  Its cells are linear or logarithmic,
-        // whichever puts fewer pairs of adjacent distinct splitters into one
-        // cell (each such pair is a bucket whose keys all need the binary
-        // search); with more than L/16 such pairs either way, or a tree of
-        // fewer than kLutMinLevels levels (a few comparisons), the stripe
-        // keeps the tree descent.  lut_mode: 0 descent, 1 linear, 2 logarithmic.
-        const int L = 1 << logL;
-        const u64 lbase = s_spl[1], ltop = s_spl[L - 1];
-        const u32 lsh = lut_shift(lbase, ltop);
-        int lut_mode = 0;
-        {
-            int crowd_lin = 0, crowd_log = 0;
-            if (tid >= 1 && tid + 1 < L) {
-                const u64 a = s_spl[tid], b = s_spl[tid + 1];
-                if (a != b) {
-                    crowd_lin = lut_cell(a, lbase, lsh) == lut_cell(b, lbase, lsh) ? 1 : 0;
-                    crowd_log = lut_cell_log(a, lbase) == lut_cell_log(b, lbase) ? 1 : 0;
-                }
-            }
-            const int n_lin = __syncthreads_count(crowd_lin);
-            const int n_log = __syncthreads_count(crowd_log);
-            if (logL >= kLutMinLevels && (n_lin * 16 <= L || n_log * 16 <= L)) lut_mode = n_lin <= n_log ? 1 : 2;
-        }
-        if (lut_mode != 0) {
-            // i(first key of every cell) by the tree descent into the (still
-            // free) grouping area, then the (lo, hi) entries
-            constexpr int CPT = kLutCells / TPB;
-            unsigned char* s_lo = (unsigned char*)grp;
-            u64 ck[CPT];
-            int ci[CPT];
-            bool ok[CPT];
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) {
-                const u32 c = (u32)(tid + q * TPB);
-                ok[q] = lut_mode == 1 ? lut_cell_start(c, lbase, lsh, &ck[q]) : lut_cell_start_log(c, lbase, &ck[q]);
-                if (!ok[q]) ck[q] = ltop;
-            }
-            classify_many<CPT>(ck, s_thi, s_tlo, s_spl, logL, false, ci);
-#pragma unroll
-            for (int q = 0; q < CPT; ++q) s_lo[tid + q * TPB] = (unsigned char)(ok[q] ? ci[q] : L - 1);
-            __syncthreads();
-            for (int c = tid; c <= kLutCells; c += TPB) {
-                u32 ent = 0;                          // cell kLutCells: keys below s_1
-                if (c < kLutCells) ent = (u32)s_lo[c] | ((c + 1 < kLutCells ? (u32)s_lo[c + 1] : (u32)(L - 1)) << 8);
-                s_lut[c] = (unsigned short)ent;
-            }
-            __syncthreads();
-        }
 
-        E nx[IPT];
-        auto load_tile = [&](u32 tn) {
-            const u32 tb = tn * TILE;
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                const u32 idx = tid + q * TPB;
-                if (tb + idx < len) nx[q] = S[tb + idx];
+    const StripeDesc sd = ws.stripes[s];
+    const SubDesc sub = ws.subs[sd.sub];
+    const int logL = (int)sub.log_leaves;
+    const bool eq = sub.eq != 0;
+    u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
+    u32* s_tlo = s_thi + kMaxLeaves;
+    for (int i = tid; i < kMaxLeaves; i += TPB) {
+        const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
+        s_thi[i] = (u32)(a >> 32);
+        s_tlo[i] = (u32)a;
+        s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
+    }
+    for (int b = tid; b < kMaxBuckets; b += TPB) {
+        s_fill[b] = 0;
+        s_cnt[b] = 0;
+        s_cnt[kMaxBuckets + b] = 0;
+        s_total[b] = 0;
+    }
+    E* A = arr + sd.begin;
+    const E* S = src + sd.begin;                 // the stripe's input: A itself, or a copy elsewhere
+    const u32 len = (u32)(sd.end - sd.begin);    // a stripe holds < 2^32 elements
+    const u32 ntiles = (len + TILE - 1) / TILE;
+    const bool g16 = ((uintptr_t)A & 15) == 0;   // block stores as 16-byte chunks
+    __syncthreads();
+    // The splitter lookup table.  Its cells are linear (aligned to multiples
+    // of 2^shift of the key domain) or logarithmic, whichever puts fewer pairs
+    // of adjacent distinct splitters into one cell (each such pair is a bucket
+    // whose keys all need the binary search); with more than L/16 such pairs
+    // either way, or a tree of fewer than kLutMinLevels levels (a few
+    // comparisons), the stripe keeps the tree descent.  lut_mode: 0 descent,
+    // 1 linear, 2 logarithmic, 3 linear with the cell taken from the key's
+    // high 32 bits (shift >= 32).
+    const int L = 1 << logL;
+    const u64 lbase = s_spl[1], ltop = s_spl[L - 1];
+    const u32 lsh = lut_abs_shift(lbase, ltop);
+    const u64 lc0 = lbase >> lsh;
+    int lut_mode = 0;
+    {
+        int crowd_lin = 0, crowd_log = 0;
+        if (tid >= 1 && tid + 1 < L) {
+            const u64 a = s_spl[tid], b = s_spl[tid + 1];
+            if (a != b) {
+                crowd_lin = lut_cell_abs(a, lc0, lsh) == lut_cell_abs(b, lc0, lsh) ? 1 : 0;
+                crowd_log = lut_cell_log(a, lbase) == lut_cell_log(b, lbase) ? 1 : 0;
             }
-        };
-        if (ntiles > 0) load_tile(0);
-        for (u32 t = 0; t < ntiles; ++t) {
-            E e[IPT];
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) e[q] = nx[q];
-            // the next tile's loads stay in flight while this one is processed
-            if (t + 1 < ntiles) load_tile(t + 1);
-            E* tile = grp;
-            const u32 tb = t * TILE;
-            const u32 tcount = len - tb < (u32)TILE ? len - tb : (u32)TILE;
-            int bk[IPT];
-            u32 rk[IPT];
-            if (lut_mode == 1) {
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const K kq = T::key(e[q]);
-                    const int i = lut_refine(kq, s_lut[lut_cell(kq, lbase, lsh)], s_spl);
-                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
-                }
-            } else if (lut_mode == 2) {
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) {
-                    const K kq = T::key(e[q]);
-                    const int i = lut_refine(kq, s_lut[lut_cell_log(kq, lbase)], s_spl);
-                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
-                }
-            } else if constexpr (std::is_same<E, K>::value) {
-                // the keys replace the elements for the descent (one fewer
-                // register array), which the inverse map then restores
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) e[q] = T::key(e[q]);
-                classify_many<IPT>(e, s_thi, s_tlo, s_spl, logL, eq, bk);
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) e[q] = T::unkey(e[q]);
-            } else {
-                K k[IPT];
-#pragma unroll
-                for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
-                classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
-            }
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                if (tid + q * TPB >= tcount) bk[q] = -1;
-                // rank within the tile's run of the bucket; a warp whose lanes
-                // all hit one bucket (long runs, repeated keys) takes one atomic
-                const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
-                u32 r;
-                if (__all_sync(0xffffffffu, bk[q] == b0)) {
-                    u32 base = 0;
-                    if (lane == 0 && b0 >= 0) base = atomicAdd(&s_cnt[b0], 32u);
-                    r = __shfl_sync(0xffffffffu, base, 0) + lane;
-                } else {
-                    r = bk[q] >= 0 ? atomicAdd(&s_cnt[bk[q]], 1u) : 0u;
-                }
-                // bucket and rank in one register: bucket << 16 | rank (rank < TILE)
-                rk[q] = bk[q] >= 0 ? ((u32)bk[q] << 16) | r : 0xffffffffu;
-            }
-            __syncthreads();
-            // Buckets whose buffer block fills in this tile emit full blocks;
-            // their new elements are grouped in the (now free) staging slot.
-            // The new elements of every other bucket go straight into its
-            // buffer block.
-            u32 c = 0, f = 0, nfull = 0;
-            if (tid < kMaxBuckets) {
-                c = s_cnt[tid];
-                f = s_fill[tid];
-                nfull = (f + c) / B;
-            }
-            // one scan of three packed counts: [tile offset 32 | blocks 16 | emitting buckets 16]
-            u64 tot;
-            const u64 pre = block_exclusive_scan<u64>(((u64)(nfull ? c : 0u) << 32) | ((u64)nfull << 16) |
-                                                          (nfull ? 1u : 0u),
-                                                      s_misc, &tot);
-            const u32 tot_blocks = (u32)((tot >> 16) & 0xffffu);
-            const u32 n_emit = (u32)(tot & 0xffffu);
-            if (tid < kMaxBuckets) {
-                const u32 bpre = (u32)((pre >> 16) & 0xffffu);
-                s_off[tid] = nfull ? (u32)(pre >> 32) : 0xffffffffu;
-                s_dst[tid] = nfull ? (u32)(C::off_grp / sizeof(E)) + (u32)(pre >> 32) : (u32)tid * B + f;
-                s_bscan[tid] = bpre;
-                for (u32 q = 0; q < nfull; ++q) s_blkb[bpre + q] = (unsigned short)tid;
-                if (nfull) s_emit[(u32)(pre & 0xffffu)] = (unsigned short)tid;
-            }
-            __syncthreads();
-#pragma unroll
-            for (int q = 0; q < IPT; ++q)
-                if (rk[q] != 0xffffffffu) s_elem[s_dst[rk[q] >> 16] + (rk[q] & 0xffffu)] = e[q];
-            __syncthreads();
-            // write full blocks over the front of the stripe
-            for (u32 i = warp; i < tot_blocks; i += NW) {
-                const u32 b = s_blkb[i];
-                const u32 jb = i - s_bscan[b];
-                const u32 fb = s_fill[b];
-                const u32 ob = s_off[b];
-                const u32 dst = (front + i) * B;
-                if (dst + B <= len) {
-                    E* g = A + dst;
-#pragma unroll
-                    for (int v = lane; v < B; v += 32) {
-                        const u32 vv = jb * B + v;
-                        g[v] = vv < fb ? buf[b * B + vv] : tile[ob + vv - fb];
-                    }
-                } else if (lane == 0) {
-                    set_status(ws.ctr, kStatusInternal);
-                }
-            }
-            __syncthreads();
-            // the remainder of a bucket that emitted blocks goes back into its
-            // buffer block (one warp per such bucket)
-            for (u32 i = warp; i < n_emit; i += NW) {
-                const u32 b = s_emit[i];
-                const u32 fb = s_fill[b], cb = s_cnt[b];
-                const u32 nf = (fb + cb) / B, rem = (fb + cb) % B;
-                const u32 from = s_off[b] + nf * B - fb;
-                for (u32 v = lane; v < rem; v += 32) buf[b * B + v] = tile[from + v];
-            }
-            __syncthreads();
-            if (tid < kMaxBuckets) {
-                s_total[tid] += c;
-                s_fill[tid] = (f + c) % B;
-                s_cnt[tid] = 0;
-            }
-            front += tot_blocks;
-            __syncthreads();
         }
-        // counts, leftovers (partially filled buffers) to the stripe's pool area
-        u32 f = tid < kMaxBuckets ? s_fill[tid] : 0;
-        u32 ltot;
-        u32 lpre = block_exclusive_scan<u32>(f, (u32*)s_misc, &ltot);
-        if (tid < kMaxBuckets) {
-            ws.counts[(u64)s * kMaxBuckets + tid] = s_total[tid];
-            ws.lscan[(u64)s * kMaxBuckets + tid] = lpre;
-            s_off[tid] = lpre;
+        const int n_lin = __syncthreads_count(crowd_lin);
+        const int n_log = __syncthreads_count(crowd_log);
+        if (logL >= kLutMinLevels && (n_lin * 16 <= L || n_log * 16 <= L)) lut_mode = n_lin <= n_log ? 1 : 2;
+        if (lut_mode == 1 && lsh >= 32) lut_mode = 3;
+    }
+    if (lut_mode != 0) {
+        // i(first key of every cell) by the tree descent into the (still
+        // free) grouping area, then the (lo, hi) entries
+        constexpr int CPT = kLutCells / TPB;
+        unsigned char* s_lo = (unsigned char*)grp;
+        u64 ck[CPT];
+        int ci[CPT];
+        bool ok[CPT];
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            const u32 c = (u32)(tid + q * TPB);
+            ok[q] = lut_mode == 2 ? lut_cell_start_log(c, lbase, &ck[q]) : lut_cell_start_abs(c, lc0, lsh, &ck[q]);
+            if (!ok[q]) ck[q] = ltop;
         }
+        classify_many<CPT>(ck, s_thi, s_tlo, s_spl, logL, false, ci);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) s_lo[tid + q * TPB] = (unsigned char)(ok[q] ? ci[q] : L - 1);
         __syncthreads();
-        if (ltot <= sd.pool_cap) {
-            for (int b = warp; b < kMaxBuckets; b += NW) {
-                const u32 fb = s_fill[b], ob = s_off[b];
-                for (u32 v = lane; v < fb; v += 32) ws.pool[sd.pool_off + ob + v] = buf[b * B + v];
-            }
-        } else if (tid == 0) {
-            set_status(ws.ctr, kStatusInternal);
+        for (int c = tid; c <= kLutCells; c += TPB) {
+            u32 ent = 0;                          // cell kLutCells (logarithmic map): keys below s_1
+            if (c < kLutCells) ent = (u32)s_lo[c] | ((c + 1 < kLutCells ? (u32)s_lo[c + 1] : (u32)(L - 1)) << 8);
+            s_lut[c] = (unsigned short)ent;
         }
-        if (tid == 0) ws.stripe_full[s] = front;
         __syncthreads();
     }
+
+    E e[IPT], nx[IPT];
+    u32 rk[IPT];
+    auto load_tile = [&](u32 tn) {
+        const u32 tb = tn * TILE;
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            const u32 idx = tid + q * TPB;
+            if (tb + idx < len) nx[q] = S[tb + idx];
+        }
+    };
+    // buckets of the tile's elements and their ranks (bucket << 16 | rank)
+    auto classify_rank = [&](u32 tn, u32* cnt) {
+        const u32 tcount = len - tn * TILE < (u32)TILE ? len - tn * TILE : (u32)TILE;
+        int (&bk)[IPT] = *reinterpret_cast<int(*)[IPT]>(&rk);   // the buckets, then bucket << 16 | rank
+        if (lut_mode == 3) {
+            const u32 c0 = (u32)lc0, shh = lsh - 32;
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const K kq = T::key(e[q]);
+                const int i = lut_refine(kq, s_lut[lut_cell_abs_hi((u32)(kq >> 32), c0, shh)], s_spl);
+                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+            }
+        } else if (lut_mode == 1) {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const K kq = T::key(e[q]);
+                const int i = lut_refine(kq, s_lut[lut_cell_abs(kq, lc0, lsh)], s_spl);
+                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+            }
+        } else if (lut_mode == 2) {
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) {
+                const K kq = T::key(e[q]);
+                const int i = lut_refine(kq, s_lut[lut_cell_log(kq, lbase)], s_spl);
+                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+            }
+        } else if constexpr (std::is_same<E, K>::value) {
+            // the keys replace the elements for the descent (one fewer
+            // register array), which the inverse map then restores
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) e[q] = T::key(e[q]);
+            classify_many<IPT>(e, s_thi, s_tlo, s_spl, logL, eq, bk);
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) e[q] = T::unkey(e[q]);
+        } else {
+            K k[IPT];
+#pragma unroll
+            for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
+            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+        }
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) {
+            if (tid + q * TPB >= tcount) bk[q] = -1;
+            // rank within the tile's run of the bucket; a warp whose lanes
+            // all hit one bucket (long runs, repeated keys) takes one atomic
+            const int b0 = __shfl_sync(0xffffffffu, bk[q], 0);
+            u32 r;
+            if (__all_sync(0xffffffffu, bk[q] == b0)) {
+                u32 base = 0;
+                if (lane == 0 && b0 >= 0) base = atomicAdd(&cnt[b0], 32u);
+                r = __shfl_sync(0xffffffffu, base, 0) + lane;
+            } else {
+                r = bk[q] >= 0 ? atomicAdd(&cnt[bk[q]], 1u) : 0u;
+            }
+            rk[q] = bk[q] >= 0 ? ((u32)bk[q] << 16) | r : 0xffffffffu;
+        }
+    };
+    // Phase A, warp 0: destinations, block descriptors and fill levels of
+    // the tile whose counts are cnt (set par); lane l handles 8 buckets.
+    u32 front = 0;                               // full blocks written at the stripe front (warp 0's count)
+    auto scan_tile = [&](u32 par) {
+        constexpr int BPL = kMaxBuckets / 32;
+        u32* cnt = s_cnt + par * kMaxBuckets;
+        uint2* binfo = s_binfo + par * kMaxBuckets;
+        u32* desc = s_desc + par * C::MAXBLK;
+        const int b0 = lane * BPL;
+        // run sizes in the grouping area (even, room for the parity pad) and blocks
+        u32 mine = 0;
+#pragma unroll
+        for (int j = 0; j < BPL; j += 4) {
+            const uint4 cv = *(const uint4*)(cnt + b0 + j), fv = *(const uint4*)(s_fill + b0 + j);
+            const u32 cc[4] = {cv.x, cv.y, cv.z, cv.w}, ff[4] = {fv.x, fv.y, fv.z, fv.w};
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const u32 nf = (ff[h] + cc[h]) / B;
+                mine += (nf ? ((cc[h] + (ff[h] & 1u) + 1u) & ~1u) : 0u) | (nf << 16);
+            }
+        }
+        u32 x = mine;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const u32 y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
+        }
+        const u32 tot = __shfl_sync(0xffffffffu, x, 31);
+        u32 off = (x - mine) & 0xffffu, blk = (x - mine) >> 16;
+        for (int j = 0; j < BPL; ++j) {
+            const u32 b = (u32)(b0 + j), cj = cnt[b], fj = s_fill[b], t = fj + cj, nf = t / B, rem = t - nf * B;
+            if (nf) {
+                const u32 p = off + (fj & 1u);       // p - f is even: the run's blocks are 16-byte aligned
+                s_dst[b] = GRP0 + p;
+                binfo[b] = make_uint2((p - fj + 64u) | (fj << 16) | (rem << 24), nf);
+                for (u32 q = 0; q < nf; ++q) desc[blk + q] = b | (q << 8);
+                blk += nf;
+                off += (cj + (fj & 1u) + 1u) & ~1u;
+            } else {
+                s_dst[b] = b * B + fj;
+            }
+            s_fill[b] = rem;
+            s_total[b] += cj;
+            cnt[b] = 0;
+        }
+        if (lane == 0) {
+            s_misc[par] = tot >> 16;
+            s_misc[2 + par] = front;
+        }
+        front += tot >> 16;
+    };
+    // Full blocks of the tile of set par, block i by warp w0 + i (step nw):
+    // a block is 512 bytes, one 16-byte chunk per lane.  The first block of a
+    // bucket starts with the f elements its buffer block held; the warp that
+    // writes it then copies the bucket's remainder back into the buffer.
+    auto write_blocks = [&](u32 par, u32 w0, u32 nw) {
+        const uint2* binfo = s_binfo + par * kMaxBuckets;
+        const u32* desc = s_desc + par * C::MAXBLK;
+        const u32 nblk = s_misc[par], fr = s_misc[2 + par];
+        for (u32 i = w0; i < nblk; i += nw) {
+            const u32 d = desc[i], b = d & 0xffu, q = d >> 8;
+            const uint2 bi = binfo[b];
+            const int vs = (int)(bi.x & 0xffffu) - 64;           // grouping index of block 0's element 0
+            const u32 f = q == 0 ? (bi.x >> 16) & 0xffu : 0u;
+            const u32 slot = fr + i;
+            if ((u64)(slot + 1) * B > len) {
+                if (lane == 0) set_status(ws.ctr, kStatusInternal);
+                continue;
+            }
+            const u32 v0 = (u32)lane * CH;
+            const E* from = v0 < f ? buf + b * B + v0 : grp + (vs + (int)(q * B) + (int)v0);
+            E* to = A + (size_t)slot * B + v0;
+            if constexpr (CH == 2) {
+                u64 x0, x1;
+                if (v0 + 1 == f) {                                 // the chunk straddles buffer and run
+                    x0 = buf[b * B + v0];
+                    x1 = grp[vs + (int)v0 + 1];
+                } else {
+                    const ulonglong2 v = *(const ulonglong2*)from;
+                    x0 = v.x;
+                    x1 = v.y;
+                }
+                if (g16) {
+                    *(ulonglong2*)to = make_ulonglong2(x0, x1);
+                } else {
+                    to[0] = x0;
+                    to[1] = x1;
+                }
+            } else {
+                *(uint4*)to = *(const uint4*)from;
+            }
+            const u32 rem = bi.x >> 24;
+            if (q == 0 && rem > 0) {
+                __syncwarp();                                      // block 0 has read the buffer
+                const E* rs = grp + (vs + (int)(bi.y * B) + (int)v0);
+                if (v0 < rem) *(uint4*)(buf + b * B + v0) = *(const uint4*)rs;
+            }
+        }
+    };
+
+    if (ntiles > 0) load_tile(0);
+    for (u32 t = 0; t < ntiles; ++t) {
+        const u32 par = t & 1u;
+        // C: this tile's buckets and ranks (its loads were issued a tile ago)
+#pragma unroll
+        for (int q = 0; q < IPT; ++q) e[q] = nx[q];
+        if (t + 1 < ntiles) load_tile(t + 1);
+        classify_rank(t, s_cnt + par * kMaxBuckets);
+        __syncthreads();
+        // A: scan of this tile by warp 0; blocks of the previous tile by the others
+        if (warp == 0) scan_tile(par);
+        else if (t > 0) write_blocks(par ^ 1u, (u32)warp - 1u, NW - 1u);
+        __syncthreads();
+        // B: scatter into buffer blocks and grouping runs
+#pragma unroll
+        for (int q = 0; q < IPT; ++q)
+            if (rk[q] != 0xffffffffu) s_elem[s_dst[rk[q] >> 16] + (rk[q] & 0xffffu)] = e[q];
+        __syncthreads();
+    }
+    if (ntiles > 0) {
+        write_blocks((ntiles - 1) & 1u, (u32)warp, NW);
+        __syncthreads();
+    }
+    // counts, leftovers (partially filled buffers) to the stripe's pool area
+    u32 f = tid < kMaxBuckets ? s_fill[tid] : 0;
+    u32 ltot;
+    u32* s_off = s_dst;                          // free now: leftover offsets
+    u32 lpre = block_exclusive_scan<u32>(f, s_desc, &ltot);
+    if (tid < kMaxBuckets) {
+        ws.counts[(u64)s * kMaxBuckets + tid] = s_total[tid];
+        ws.lscan[(u64)s * kMaxBuckets + tid] = lpre;
+        s_off[tid] = lpre;
+    }
+    __syncthreads();
+    if (ltot <= sd.pool_cap) {
+        for (int b = warp; b < kMaxBuckets; b += NW) {
+            const u32 fb = s_fill[b], ob = s_off[b];
+            for (u32 v = lane; v < fb; v += 32) ws.pool[sd.pool_off + ob + v] = buf[b * B + v];
+        }
+    } else if (tid == 0) {
+        set_status(ws.ctr, kStatusInternal);
+    }
+    if (tid == 0) {
+        u32 fr = 0;
+        if (ntiles > 0) fr = s_misc[2 + ((ntiles - 1) & 1u)] + s_misc[(ntiles - 1) & 1u];
+        ws.stripe_full[s] = fr;
+    }
+    __syncthreads();
 }
 
 // src: where the elements of the stripes are read (arr itself for the usual
@@ -893,7 +977,7 @@ struct PermuteCfg {
     static constexpr int V = 8;                  // movers per warp (lanes 0..V-1)
     static constexpr int MIN_CTAS = 6;           // register bound; shared memory admits 5 per SM (160 movers)
     static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block copy
-    static constexpr int MAX_MOVERS_PER_BUCKET = 64;
+    static constexpr int MAX_MOVERS_PER_BUCKET = 128;
     // block buffers of the warps, then one copy of the subproblem's tables
     // shared by the CTA (all its warps move blocks of the same subproblem)
     static constexpr size_t off_buf = 0;                                          // E[NW][2][V][B]
@@ -954,21 +1038,38 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
     bool exw_valid = false;
     for (;;) {
         if (!__any_sync(0xffffffffu, !done) || failed) break;
-        // ---- one claim per active mover
+        // ---- one claim per active mover.  The read claims of the lanes that
+        // share a primary bucket are one atomic (r - count, readers + 1): the
+        // lane of rank q in the group reads block r - q, and the group holds
+        // one reader count until the warp has loaded its blocks, so the count
+        // is bounded by the warps of a subproblem, not by its movers.
         u64 old = 0;
-        if (!done) {
-            if (have) old = atom_add_acquire(&wr[tgt], kClaimWrite);
-            else old = atomicAdd(&wr[prim], kClaimRead);
+        const bool rclaim = !done && !have;
+        const unsigned rmask = __ballot_sync(0xffffffffu, rclaim);
+        u32 rrank = 0;
+        bool holds_reader = false;
+        if (rclaim) {
+            const unsigned grp = __match_any_sync(rmask, prim);
+            const int lead = __ffs(grp) - 1;
+            rrank = (u32)__popc(grp & ((1u << lane) - 1u));
+            u64 o = 0;
+            if (lane == lead) o = atomicAdd(&wr[prim], 1ull - ((u64)__popc(grp) << kRdBits));
+            old = __shfl_sync(grp, o, lead);
+            if (lane == lead) {
+                if (pk_r(old) < pk_w(old)) red_add_relaxed64(&wr[prim], kReadDone);   // no lane got a block: undo
+                else holds_reader = true;
+            }
+        } else if (!done) {
+            old = atom_add_acquire(&wr[tgt], kClaimWrite);
         }
-        const long long w = pk_w(old), r = pk_r(old);
+        const long long w = pk_w(old), r = pk_r(old) - (long long)rrank;
         const u32 rd = pk_readers(old);
         bool ldn = false, ldt = false, emp = false, exd = false;
         u64 slot = 0;
         if (!done) {
             if (!have) {
                 if (r < w) {
-                    // no unprocessed block left in the primary bucket: undo
-                    red_add_relaxed64(&wr[prim], kReadDone);
+                    // no unprocessed block left in the primary bucket
                     atomicOr(&exh[prim >> 5], 1u << (prim & 31));
                     exd = true;
                 } else {
@@ -1012,7 +1113,7 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
         // a slot that is still being read.  Counts are dropped before this
         // warp waits on any count, so movers of one warp never wait on each
         // other.
-        if (ldn) red_add_release64(&wr[prim], kReadDone);
+        if (holds_reader) red_add_release64(&wr[prim], kReadDone);
         // ---- writes into empty slots (after the reader counts drained)
         bool ok = true;
         if (emp && rd != 0) {
@@ -1119,7 +1220,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
                     u64 x = (bl * (u64)G + total - 1) / total;
                     const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + MOV - 1) / MOV;
                     const u64 cap_k = (bl + MOV - 1) / MOV;
-                    const u64 cap_r = kMaxMoversPerSub / MOV;
+                    const u64 cap_r = kMaxReadersPerSub / NW;
                     x = x < cap_b ? x : cap_b;
                     x = x < cap_k ? x : cap_k;
                     x = x < cap_r ? x : cap_r;

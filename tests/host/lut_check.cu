@@ -9,7 +9,9 @@
 // the first key of sampled cells +- 1, the ends of the key domain and random
 // keys.  The table is built exactly as the kernel builds it: lo_c from the
 // first key of cell c, hi_c = lo_{c+1} (L - 1 for the last cell), the extra
-// entry (0, 0) for keys below s_1.  Prints "ok <keys checked>" and exits 0,
+// entry (0, 0) for keys below s_1 (relative maps).  The absolute linear map
+// (cells aligned to multiples of 2^shift, cell 0 starting at key 0) is
+// checked in both its 64-bit and its 32-bit high-word form.  Prints "ok <keys checked>" and exits 0,
 // or prints the first mismatch and exits 1.
 #include <algorithm>
 #include <cmath>
@@ -60,11 +62,27 @@ int main(int argc, char** argv) {
             std::printf("shift %u leaves the range wider than the table\n", sh);
             return 1;
         }
-        for (int mode = 1; mode <= 2; ++mode) {
+        // map 3: linear cells aligned in the key domain (absolute), with the
+        // 32-bit high-word form wherever the shift allows it
+        const u32 ash = lut_abs_shift(base, top);
+        const u64 ac0 = base >> ash;
+        if ((top >> ash) - ac0 >= (u64)kLutCells) {
+            std::printf("absolute shift %u leaves the range wider than the table\n", ash);
+            return 1;
+        }
+        for (int mode = 1; mode <= 3; ++mode) {
             auto start = [&](u32 cc, u64* st) {
+                if (mode == 3) return lut_cell_start_abs(cc, ac0, ash, st);
                 return mode == 1 ? lut_cell_start(cc, base, sh, st) : lut_cell_start_log(cc, base, st);
             };
-            auto cell = [&](u64 e) { return mode == 1 ? lut_cell(e, base, sh) : lut_cell_log(e, base); };
+            auto cell = [&](u64 e) -> u32 {
+                if (mode == 3) {
+                    const u32 c = lut_cell_abs(e, ac0, ash);
+                    if (ash >= 32 && lut_cell_abs_hi((u32)(e >> 32), (u32)ac0, ash - 32) != c) return kLutCells + 7;
+                    return c;
+                }
+                return mode == 1 ? lut_cell(e, base, sh) : lut_cell_log(e, base);
+            };
             std::vector<unsigned char> lo(kLutCells);
             for (u32 cc = 0; cc < (u32)kLutCells; ++cc) {
                 u64 st;
@@ -75,6 +93,10 @@ int main(int argc, char** argv) {
                 u32 ent = 0;
                 if (cc < kLutCells) ent = (u32)lo[cc] | ((cc + 1 < kLutCells ? (u32)lo[cc + 1] : (u32)(L - 1)) << 8);
                 lut[cc] = (unsigned short)ent;
+            }
+            if (mode == 3 && lo[0] != (unsigned char)count_le(spl, L, 0)) {
+                std::printf("absolute map: cell 0 does not start at key 0\n");
+                return 1;
             }
             std::vector<u64> keys = {0ull, ~0ull, base, top, base - 1, top + 1};
             for (int t = 1; t < L; ++t) {
@@ -94,9 +116,11 @@ int main(int argc, char** argv) {
                 keys.push_back(rng());
                 keys.push_back(top > base ? base + rng() % (top - base) : base);
             }
+            if (mode == 3)
+                for (int r = 0; r < 200; ++r) keys.push_back(base > 0 ? rng() % base : 0);   // below s_1
             for (u64 e : keys) {
                 const u32 ce = cell(e);
-                if (ce > (u32)kLutCells) {
+                if (ce > (u32)kLutCells || (mode == 3 && ce >= (u32)kLutCells)) {
                     std::printf("cell %u out of range (map %d, key %llu)\n", ce, mode, e);
                     return 1;
                 }
