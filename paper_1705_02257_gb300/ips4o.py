@@ -16,7 +16,9 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libips4o_gb300.so")
+# IPS4O_LIBRARY names another build of the same library (e.g. one compiled
+# with different tuning constants); by default the in-tree build is loaded.
+LIB_PATH = os.environ.get("IPS4O_LIBRARY") or os.path.join(_HERE, "libips4o_gb300.so")
 
 U64, F64, PAIR_U64, REC100_K10 = 0, 1, 2, 3
 KEY_TYPES = {"u64": U64, "f64": F64, "pair": PAIR_U64, "rec100": REC100_K10}
