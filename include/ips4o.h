@@ -25,14 +25,15 @@
  *     plus a small host staging area.
  *   - Calls on the same (device, stream) are serialised by the library;
  *     calls on different streams, made from different host threads, run
- *     side by side on the device, each with its own workspace.  Calls are not
- *     capturable in a CUDA graph: the host driver reads the number of
- *     subproblems of each recursion level back from the device before it
- *     launches the next level (ips4o_sort_segmented_async is the exception).
+ *     side by side on the device, each with its own workspace.  ips4o_sort
+ *     and ips4o_sort_segmented_async only enqueue work (capturable in a CUDA
+ *     graph with a reserved workspace); the other sort calls plan each
+ *     recursion level on the host and synchronise the stream per level.
  *   - Return codes: argument errors are detected before any work is queued;
  *     device-side errors (an exhausted bounded wait, a broken internal
- *     invariant) are reported by the call that detects them through the
- *     device status word, which is read at each level.
+ *     invariant) are recorded in a device status word, which the
+ *     synchronising calls read at each level and ips4o_stream_status reads
+ *     for the enqueue-only ones.
  */
 #ifndef IPS4O_GB300_H
 #define IPS4O_GB300_H
@@ -142,8 +143,25 @@ typedef struct {
 } ips4o_stats;
 
 /* Sort d_ptr[0..n) in place (Section 4: recursive distribution steps down
- * to the base case).  n in {0, 1} is a no-op.  Synchronises the stream once
- * per recursion level; on return the sort has completed on the device. */
+ * to the base case).  n in {0, 1} is a no-op.
+ * Asynchronous: the call only enqueues kernels on `stream` and returns; the
+ * recursion levels are planned on the device (each round takes the next
+ * chunk of a level's subproblems from a queue in device memory), so the host
+ * never waits.  Work on the stream after the call sees the sorted array.
+ *   - Argument errors are returned at once, before anything is queued.
+ *   - Device-side errors (a bounded wait that gave up, a failed invariant
+ *     check) are returned by ips4o_stream_status(stream), which waits for
+ *     the stream; after such an error d_ptr holds the same elements,
+ *     permuted but not sorted.  ips4o_get_stats also waits for the call.
+ *   - The workspace of (current device, stream) grows on the first call of a
+ *     size (cudaMalloc).  Reserved beforehand with ips4o_reserve_workspace(n,
+ *     1, key_type, stream), a call allocates nothing and can be captured into
+ *     a CUDA graph; under capture without a large enough reservation it
+ *     returns IPS4O_ERR_TOO_LARGE and queues nothing.
+ *   - Extra device memory (Theorem 2): a leftover pool for 4 stripes per SM
+ *     (independent of n) plus per-chunk tables, two level queues of
+ *     n / (base-case size) entries, and the segment scheduler's per-CTA
+ *     areas; see ips4o_workspace_bytes. */
 ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream);
 
 /* Same as ips4o_sort but for an array in HOST memory: the elements are
@@ -224,9 +242,9 @@ ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t 
 
 /* Waits for all work on `stream` and reports a CUDA error that it raised
  * (IPS4O_ERR_CUDA, text in ips4o_last_cuda_error), then the device status
- * word of the last ips4o_sort_segmented_async call on the stream
- * (IPS4O_ERR_TIMEOUT, IPS4O_ERR_INTERNAL), else IPS4O_OK.  The other sort
- * calls return device-side errors themselves. */
+ * word of the last ips4o_sort or ips4o_sort_segmented_async call on the
+ * stream (IPS4O_ERR_TIMEOUT, IPS4O_ERR_INTERNAL), else IPS4O_OK.  The other
+ * sort calls return device-side errors themselves. */
 ips4o_status ips4o_stream_status(void* stream);
 
 /* Sort d_ptr[0..n) in place, like ips4o_sort, without allocating any memory.

@@ -100,9 +100,65 @@ DeviceState* stream_state(void* stream, cudaError_t* err) {
 
 DeviceState* current_device_state(cudaError_t* err) { return stream_state(nullptr, err); }
 
-static void publish_stats(const DeviceState& st) {
+static DeviceState* g_last_state[64];
+
+static void publish_stats(DeviceState& st) {
     std::lock_guard<std::mutex> lk(g_mtx);
     g_last_stats[st.device] = st.stats;
+    g_last_state[st.device] = &st;
+}
+
+ips4o_status collect_profile_events(DeviceState& st) {
+    for (const DeviceState::Timed& t : st.timed) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, st.events[t.ev], st.events[t.ev + 1]);
+        if (e != cudaSuccess) {
+            set_last_cuda_error(e, "cudaEventElapsedTime");
+            st.timed.clear();
+            st.next_event = 0;
+            return IPS4O_ERR_CUDA;
+        }
+        st.stats.phase_ms[t.phase] += ms;
+        st.stats.phase_launches[t.phase]++;
+    }
+    st.timed.clear();
+    st.next_event = 0;
+    return IPS4O_OK;
+}
+
+ips4o_status finalize_pending(DeviceState& st) {
+    if (!st.pending) return IPS4O_OK;
+    st.pending = false;
+    cudaError_t e = cudaStreamSynchronize(st.pending_stream);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaStreamSynchronize");
+        return IPS4O_ERR_CUDA;
+    }
+    LoopState h;
+    e = cudaMemcpy(&h, st.pending_ls, sizeof h, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        set_last_cuda_error(e, "cudaMemcpy(loop state)");
+        return IPS4O_ERR_CUDA;
+    }
+    st.stats.levels = h.levels;
+    st.stats.chunks = (uint32_t)h.chunks;
+    st.stats.subproblems = h.subproblems;
+    st.stats.blocks_moved = h.blocks_moved;
+    st.stats.blocks_skipped = h.blocks_skipped;
+    st.stats.fix_blocks_moved = h.fix_blocks;
+    st.stats.base_case_buckets = h.base_buckets;
+    st.stats.elements_distributed = h.elements_distributed;
+    ips4o_status rc = collect_profile_events(st);
+    publish_stats(st);
+    if (h.guard_hits) {
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "device bounds guard failed %u time(s); first at kernels line %u (%llu, %llu)",
+                      h.guard_hits, h.guard_line, (unsigned long long)h.guard_a, (unsigned long long)h.guard_b);
+        set_last_message(msg);
+    }
+    if (h.status & kStatusTimeout) return IPS4O_ERR_TIMEOUT;
+    if (h.status) return IPS4O_ERR_INTERNAL;
+    return rc;
 }
 
 ips4o_status ensure_device_buffer(void** ptr, size_t* have, size_t need) {
@@ -229,7 +285,7 @@ ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream) {
     if (rc != IPS4O_OK) return rc;
     if (n < 2) return IPS4O_OK;
     cudaError_t e;
-    DeviceState* st = current_device_state(&e);
+    DeviceState* st = stream_state(stream, &e);
     if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     std::lock_guard<std::mutex> lk(st->mtx);
     return dispatch(*st, d_ptr, n, key_type, (cudaStream_t)stream, nullptr);
@@ -363,7 +419,7 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
     }
     e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamSynchronize"); return IPS4O_ERR_CUDA; }
-    return IPS4O_OK;
+    return finalize_pending(*st);
 }
 
 ips4o_status ips4o_partition(void* d_ptr, size_t n, int key_type, void* stream, uint64_t* h_bounds,
@@ -489,6 +545,16 @@ ips4o_status ips4o_get_stats(ips4o_stats* out) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     if (dev < 0 || dev >= 64) return IPS4O_ERR_INVALID_ARG;
+    DeviceState* last = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mtx);
+        last = g_last_state[dev];
+    }
+    if (last) {
+        // an asynchronous call's counters are completed here (waits for its stream)
+        std::lock_guard<std::mutex> lk(last->mtx);
+        finalize_pending(*last);
+    }
     std::lock_guard<std::mutex> lk(g_mtx);
     *out = g_last_stats[dev];
     return IPS4O_OK;
@@ -549,6 +615,7 @@ ips4o_status ips4o_stream_status(void* stream) {
     DeviceState* st = stream_state(stream, &e);
     if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
     std::lock_guard<std::mutex> lk(st->mtx);
+    if (st->pending) return finalize_pending(*st);
     if (!st->d_status) return IPS4O_OK;
     unsigned bits = 0;
     e = cudaMemcpy(&bits, st->d_status, sizeof bits, cudaMemcpyDeviceToHost);

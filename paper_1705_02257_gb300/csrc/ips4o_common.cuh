@@ -151,6 +151,29 @@ struct ChunkCounters {
     u64 base_buckets;
 };
 
+// State of a sort whose recursion levels are planned on the device (the
+// asynchronous ips4o_sort): the subproblems of the current level are a
+// queue in device memory, each round takes the next chunk of it, and the
+// cleanup appends the buckets that must recurse to the other queue.
+struct LoopState {
+    Task* cur_q;            // subproblems of the current level
+    Task* next_q;           // subproblems of the next level (appended by the cleanup)
+    u32 cur_count;          // entries of cur_q
+    u32 cur_pos;            // entries of cur_q already planned
+    u32 next_count;         // entries of next_q
+    u32 level;
+    u32 nsub, nstr;         // the chunk of the current round
+    u32 bstride;            // cleanup tickets per subproblem of the chunk
+    u32 cta_cleanup;        // 1: one CTA per bucket in the cleanup (subproblems with many stripes)
+    u32 status;             // error bits of the whole call
+    u32 guard_line, guard_hits, levels;
+    u64 guard_a, guard_b;
+    u64 stripe_len;         // stripe length of the current level
+    u64 blocks_moved, blocks_skipped, fix_blocks, base_buckets, elements_distributed, subproblems, chunks;
+    u32 fallback_tasks;     // subproblems left to the segment scheduler after the last round
+    u32 pad;
+};
+
 // Pointers into the workspace for one key type.
 template <class T>
 struct Workspace {
@@ -182,6 +205,8 @@ struct Workspace {
     u32* hist;                // [65]            scheduler queue built on the device: size groups
     Task* stacks;             // [max_sub][stack_cap] scheduler: buckets each CTA still has to distribute
     ChunkCounters* ctr;       // [1]
+    Task* next_tasks2;        // [next_cap]      the second level queue of the device-planned recursion
+    LoopState* ls;            // [1] device-planned recursion; null when the host plans the levels
     u32 max_sub, max_stripes;
     u64 pool_cap, next_cap, init_cap, stack_cap;
 };

@@ -16,13 +16,18 @@
 
 #include "ips4o_host.h"
 #include "ips4o_kernels.cuh"
-#include "ips4o_segments.cuh"
+#include "ips4o_rounds.cuh"
 
 namespace ips4o {
 
 constexpr u32 kSpinLimit = 1u << 22;     // bounded waits: ~0.3 s with the sleeps
 constexpr int kDefaultAlpha = 16;
-constexpr u64 kMinStripe = 1u << 16;     // elements; keeps leftovers small relative to a stripe
+// Device-planned sorts: the partial buffers of at most this many stripes per
+// SM are held at once (the leftover pool, Theorem 2's O(k b t) with t a
+// multiple of the SM count, independent of n), and at most this many
+// subproblems form one round's chunk.
+constexpr u64 kRoundStripesPerSm = 4;
+constexpr u32 kRoundMaxSub = 512;
 
 inline u32 pow2_ceil_host(u64 x) {
     u32 p = 1;
@@ -36,6 +41,8 @@ struct Caps {
     u64 pool_cap, next_cap;
     u64 init_cap;       // segments that go straight to the base case (segmented calls)
     u64 stack_cap;      // segment scheduler: buckets per CTA stack (0 = not used)
+    u32 stack_slots = 0;   // segment scheduler: CTA stacks
+    bool rounds = false;   // device-planned levels: a second task queue and the loop state
 };
 
 constexpr u64 kSegStackCap = 2048;     // per CTA; a distribution step pushes at most 256 buckets
@@ -50,6 +57,7 @@ Caps<T> caps_for_scheduler(int sms, u64 num_segments) {
     c.next_cap = 16;
     c.init_cap = num_segments;
     c.stack_cap = kSegStackCap;
+    c.stack_slots = (u32)sms;
     return c;
 }
 
@@ -81,6 +89,52 @@ Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
     c.init_cap = 0;
     c.stack_cap = 0;
     return c;
+}
+
+// Workspace of a device-planned sort of n elements: a leftover pool for
+// kRoundStripesPerSm stripes per SM (or the whole input, when smaller), at
+// most kRoundMaxSub subproblems per round, two level queues for every
+// subproblem a level can have (n / (threshold + 1)), and the segment
+// scheduler's per-CTA areas for subproblems left after the last round.
+template <class T>
+Caps<T> caps_for_rounds(u64 n, int sms, u64 cap) {
+    const u64 B = T::kBlock, per = (u64)kMaxBuckets * (B - 1);
+    Caps<T> c;
+    const u64 stripes = kRoundStripesPerSm * (u64)std::max(1, sms);
+    c.max_sub = (u32)std::min<u64>(kRoundMaxSub, n / (cap + 1) + 1);
+    c.max_stripes = (u32)std::min<u64>(4096, std::max<u64>(stripes, c.max_sub));
+    c.pool_cap = std::min<u64>(stripes * per, n + (u64)kMaxBuckets * B);
+    c.pool_cap = std::max<u64>(c.pool_cap, per);
+    c.next_cap = n / (cap + 1) + 16;
+    c.init_cap = 2 * c.next_cap;
+    c.stack_cap = kSegStackCap;
+    // the segment scheduler's CTAs each take one subproblem slot, stripe
+    // slot, pool area and stack
+    c.stack_slots = (u32)std::max<u64>(1, std::min<u64>({(u64)std::max(1, sms), (u64)c.max_sub,
+                                                            (u64)c.max_stripes, c.pool_cap / per}));
+    c.rounds = true;
+    return c;
+}
+
+// CTAs of the segment scheduler that finishes a device-planned sort.
+template <class T>
+u32 fallback_grid(const Caps<T>& c) {
+    return c.stack_slots;
+}
+
+// Rounds enqueued for a device-planned sort of n elements: level l has about
+// k^(l-1) subproblems of n / k^(l-1) elements, which take ceil(k^(l-1) /
+// max_sub) rounds, down to the recursion threshold; plus one round for
+// buckets that come out larger than nominal.
+inline u32 rounds_for(u64 n, u64 cap, u32 k_max, u32 max_sub) {
+    double subs = 1.0, m = (double)n;
+    u32 r = 0;
+    while (m > (double)cap && r < 4096) {
+        r += (u32)std::ceil(subs / (double)max_sub);
+        subs *= k_max;
+        m /= k_max;
+    }
+    return r + 1;
 }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -123,8 +177,14 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.init_tasks = (Task*)take(c.init_cap * sizeof(Task));
     w.init_count = (u32*)take(4 * sizeof(u32));
     w.hist = (u32*)take(65 * sizeof(u32));
-    w.stacks = (Task*)take(S * c.stack_cap * sizeof(Task));
+    w.stacks = (Task*)take((u64)c.stack_slots * c.stack_cap * sizeof(Task));
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
+    w.next_tasks2 = c.rounds ? (Task*)take(c.next_cap * sizeof(Task)) : nullptr;
+    w.ls = c.rounds ? (LoopState*)take(sizeof(LoopState)) : nullptr;
+    if (!base) {
+        w.next_tasks2 = nullptr;
+        w.ls = nullptr;
+    }
     w.max_sub = c.max_sub;
     w.max_stripes = c.max_stripes;
     w.pool_cap = c.pool_cap;
@@ -145,8 +205,7 @@ size_t host_stage_bytes(const Caps<T>& c) {
 
 template <class T>
 size_t workspace_bytes_t(size_t n, int sms) {
-    Caps<T> c = caps_for<T>(n, sms, global_params().stripes_per_sm, recursion_cap<T>(global_params()));
-    return carve<T>(c, nullptr, nullptr);
+    return carve<T>(caps_for_rounds<T>(n, sms, recursion_cap<T>(global_params())), nullptr, nullptr);
 }
 
 // Number of leaves for a subproblem of n elements (Section 4.7, adaptive
@@ -220,9 +279,6 @@ struct Driver {
     u32 k_max;
     int permute_grid = 0;
     u64 level_stripe_len = 0;   // stripe length of the level being planned
-    int next_event = 0;
-    struct Timed { int phase; int ev; };
-    std::vector<Timed> timed;
 
     Driver(DeviceState& s, cudaStream_t strm) : st(s), stream(strm), prm(global_params()) {}
     Driver(DeviceState& s, cudaStream_t strm, const ips4o_params& p) : st(s), stream(strm), prm(p) {}
@@ -283,6 +339,10 @@ struct Driver {
         permute_grid = st.permute_grid[T::kId];
         st.stats = ips4o_stats{};
         st.stats.workspace_bytes = st.ws_bytes;
+        // a new call supersedes the statistics of an earlier asynchronous one
+        st.pending = false;
+        st.timed.clear();
+        st.next_event = 0;
         return IPS4O_OK;
     }
 
@@ -290,15 +350,15 @@ struct Driver {
     ips4o_status ev_begin(int phase, int* slot) {
         *slot = -1;
         if (!prm.profile) return IPS4O_OK;
-        while ((int)st.events.size() < next_event + 2) {
+        while ((int)st.events.size() < st.next_event + 2) {
             cudaEvent_t e;
             IPS4O_CUDA(cudaEventCreate(&e));
             st.events.push_back(e);
         }
-        *slot = next_event;
-        next_event += 2;
+        *slot = st.next_event;
+        st.next_event += 2;
         IPS4O_CUDA(cudaEventRecord(st.events[*slot], stream));
-        timed.push_back(Timed{phase, *slot});
+        st.timed.push_back(DeviceState::Timed{phase, *slot});
         return IPS4O_OK;
     }
     ips4o_status ev_end(int slot) {
@@ -307,17 +367,7 @@ struct Driver {
         IPS4O_CUDA(cudaEventRecord(st.events[slot + 1], stream));
         return IPS4O_OK;
     }
-    ips4o_status collect_events() {
-        for (const Timed& t : timed) {
-            float ms = 0.f;
-            IPS4O_CUDA(cudaEventElapsedTime(&ms, st.events[t.ev], st.events[t.ev + 1]));
-            st.stats.phase_ms[t.phase] += ms;
-            st.stats.phase_launches[t.phase]++;
-        }
-        timed.clear();
-        next_event = 0;
-        return IPS4O_OK;
-    }
+    ips4o_status collect_events() { return collect_profile_events(st); }
 #define IPS4O_LAUNCH(phase, ...)                                  \
     do {                                                          \
         int slot_;                                                \
@@ -561,6 +611,83 @@ struct Driver {
         return levels(d, std::vector<Task>{Task{0, n}}, part);
     }
 
+    // The sort as enqueued work only (Section 4's recursion planned on the
+    // device, see ips4o_rounds.cuh): no host synchronisation, so the call
+    // returns at once and can be captured in a CUDA graph.  Under capture
+    // the workspace must have been reserved (ips4o_reserve_workspace), since
+    // nothing may be allocated; otherwise it grows as needed.  Statistics and
+    // device-side errors are read back later (finalize_pending).
+    ips4o_status enqueue_sort(E* d, u64 n, const E* from = nullptr) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        IPS4O_CUDA(cudaStreamIsCapturing(stream, &cap));
+        const bool capturing = cap != cudaStreamCaptureStatusNone;
+        const u64 rc_cap = recursion_cap<T>(prm);
+        const Caps<T> c = caps_for_rounds<T>(n, st.sms, rc_cap);
+        ips4o_status rc = setup(n, 0, &c, capturing ? kEnqueue : kGrow);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = n;
+        st.d_status = &ws.ls->status;
+        if (!from) from = d;
+        if (n <= (u64)rec_cap) {
+            if (from != d) IPS4O_CUDA(cudaMemcpyAsync(d, from, n * sizeof(E), cudaMemcpyDefault, stream));
+            IPS4O_LAUNCH(7, (k_plan_base<T><<<1, 32, 0, stream>>>(ws, n)));
+            if (n <= (u64)T::kBaseTiny) {
+                IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<1, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                                    d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+            } else if (n <= (u64)T::kBaseSmall) {
+                IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                                    d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+            } else {
+                IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<1, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                                    d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+            }
+            IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+        } else {
+            PlanArgs pa;
+            pa.n = n;
+            pa.first = 1;
+            pa.k_max = k_max;
+            pa.alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
+            pa.base_cap = base_cap;
+            pa.sms = (u32)st.sms;
+            pa.w0 = (u32)std::max(1, prm.stripes_per_sm);
+            const u32 R = rounds_for(n, rc_cap, k_max, c.max_sub);
+            const u32 sms = (u32)st.sms;
+            for (u32 r = 0; r < R; ++r) {
+                pa.first = r == 0 ? 1u : 0u;
+                const E* src = r == 0 ? from : d;     // round 0 is the whole input (level 1)
+                IPS4O_LAUNCH(7, (k_plan<T><<<1, 1024, 0, stream>>>(ws, pa)));
+                IPS4O_LAUNCH(0, (k_sample<T, 512><<<2 * sms, 512, 0, stream>>>(src, ws, 0, prm.seed)));
+                IPS4O_LAUNCH(1, (k_classify<T><<<sms, ClassifyRegCfg<T>::TPB, ClassifyRegCfg<T>::smem_bytes, stream>>>(
+                                    d, src, ws, 0)));
+                IPS4O_LAUNCH(2, (k_prefix<T, 256><<<4 * sms, 256, 0, stream>>>(ws, 0)));
+                IPS4O_LAUNCH(3, (k_fix<T, 256><<<2 * sms, 256, 0, stream>>>(d, ws)));
+                IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
+                                    d, ws, 0, spin_limit())));
+                IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<2 * sms, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
+                                                    stream>>>(d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
+                IPS4O_LAUNCH(5, (k_cleanup<T><<<4 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                                    d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
+                IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                                    d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+                IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<2 * sms, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                                    d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+                IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                                    d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+            }
+            // subproblems left after the last round: the segment scheduler
+            IPS4O_LAUNCH(7, (k_rounds_done<T><<<1, 1024, 0, stream>>>(ws)));
+            const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
+            IPS4O_LAUNCH(4, (k_segments<T><<<fallback_grid<T>(c), SegCfg<T>::TPB, SegCfg<T>::smem_bytes,
+                                             stream>>>(d, ws, sq, prm.seed, k_max, spin_limit())));
+            IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+        }
+        st.pending = true;
+        st.pending_ls = ws.ls;
+        st.pending_stream = stream;
+        return IPS4O_OK;
+    }
+
     // Independent segments d[t.begin, t.begin + t.n) of one array, all sorted
     // by one call: the segments no larger than the base case are sorted in
     // shared memory straight away; the others enter the first distribution
@@ -744,19 +871,21 @@ struct Driver {
     }
 };
 
+// ips4o_sort: enqueued work (device-planned levels); ips4o_partition: one
+// host-planned distribution step whose result is read back.
 template <class T>
 ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
     Driver<T> drv(st, s);
-    return drv.run((typename T::elem_t*)d, (u64)n, part);
+    if (part) return drv.run((typename T::elem_t*)d, (u64)n, part);
+    return drv.enqueue_sort((typename T::elem_t*)d, (u64)n);
 }
 
 // d[0, n) = the sorted elements of src[0, n) (src device-accessible, e.g. the
-// device address of pinned host memory; src is only read).
+// device address of pinned host memory; src is only read), enqueued.
 template <class T>
 ips4o_status sort_from_t(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s) {
     Driver<T> drv(st, s);
-    drv.src0 = (const typename T::elem_t*)src;
-    return drv.run((typename T::elem_t*)d, (u64)n, nullptr);
+    return drv.enqueue_sort((typename T::elem_t*)d, (u64)n, (const typename T::elem_t*)src);
 }
 
 // Grow the stream's workspace and staging to what a call on n elements in
@@ -766,8 +895,9 @@ ips4o_status reserve_t(DeviceState& st, u64 n, u64 num_segments) {
     const ips4o_params& prm = global_params();
     Caps<T> c = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
     c.init_cap = num_segments;
-    const size_t need = std::max(carve<T>(c, nullptr, nullptr),
-                                 carve<T>(caps_for_scheduler<T>(st.sms, num_segments), nullptr, nullptr));
+    const size_t need = std::max({carve<T>(c, nullptr, nullptr),
+                                  carve<T>(caps_for_scheduler<T>(st.sms, num_segments), nullptr, nullptr),
+                                  carve<T>(caps_for_rounds<T>(n, st.sms, recursion_cap<T>(prm)), nullptr, nullptr)});
     ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
     if (rc != IPS4O_OK) return rc;
     if (!st.attrs_ready[T::kId] && (rc = set_kernel_attributes<T>(st)) != IPS4O_OK) return rc;

@@ -26,9 +26,27 @@ struct DeviceState {
     bool attrs_ready[4] = {false, false, false, false};   // kernel attributes set, per element type
     int permute_grid[4] = {0, 0, 0, 0};
     std::vector<cudaEvent_t> events;
+    struct Timed { int phase; int ev; };
+    std::vector<Timed> timed;       // profiled launches whose events have not been read yet
+    int next_event = 0;
+    // a device-planned (asynchronous) call whose statistics and status have
+    // not been read back yet: its loop state and stream
+    bool pending = false;
+    const void* pending_ls = nullptr;
+    cudaStream_t pending_stream = nullptr;
     std::mutex mtx;
     ips4o_stats stats{};
 };
+
+// Completes the statistics of the last asynchronous call on this state
+// (waits for its stream; reads the device loop state and the profiling
+// events) and returns the device-side status it recorded.  Callers hold
+// st.mtx.
+ips4o_status finalize_pending(DeviceState& st);
+// Kernel times of the profiled launches whose events were recorded on the
+// state (params.profile), added to its statistics.  The events must have
+// completed (the caller has synchronised the stream).
+ips4o_status collect_profile_events(DeviceState& st);
 
 // The library's default parameters (what ips4o_set_params(NULL) restores).
 constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0};

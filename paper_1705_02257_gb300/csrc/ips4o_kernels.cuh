@@ -79,9 +79,8 @@ __global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, W
     __shared__ K keys[4096];
     __shared__ K cand[256];
     __shared__ u32 scan_tmp[32];
-    const u32 j = blockIdx.x;
-    if (j >= nsub) return;
-    sample_sub<T, TPB>(arr, ws, j, seed, keys, cand, scan_tmp);
+    if (ws.ls) nsub = ws.ls->nsub;                  // device-planned round
+    for (u32 j = blockIdx.x; j < nsub; j += gridDim.x) sample_sub<T, TPB>(arr, ws, j, seed, keys, cand, scan_tmp);
 }
 
 // ------------------------------------------------- local classification
@@ -753,6 +752,7 @@ __global__ void __launch_bounds__(ClassifyRegCfg<T>::TPB, 1)
     k_classify(typename T::elem_t* arr, const typename T::elem_t* src, Workspace<T> ws, u32 nstripes) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ u32 s_stripe;
+    if (ws.ls) nstripes = ws.ls->nstr;              // device-planned round
     for (;;) {
         if (threadIdx.x == 0) s_stripe = atomicAdd(&ws.ctr->stripe_next, 1u);
         __syncthreads();
@@ -860,9 +860,11 @@ __global__ void __launch_bounds__(TPB) k_prefix(Workspace<T> ws, u32 nsub) {
     __shared__ u32 s_sbk[kMaxStripesPerSub];
     __shared__ u32 s_full[kMaxStripesPerSub];
     __shared__ u32 s_delim[kMaxBuckets + 1];
-    const u32 j = blockIdx.x;
-    if (j >= nsub) return;
-    prefix_sub<T, TPB>(ws, j, tmp64, s_sbk, s_full, s_delim);
+    if (ws.ls) nsub = ws.ls->nsub;                  // device-planned round
+    for (u32 j = blockIdx.x; j < nsub; j += gridDim.x) {
+        prefix_sub<T, TPB>(ws, j, tmp64, s_sbk, s_full, s_delim);
+        __syncthreads();
+    }
 }
 
 // -------------------------------------------- empty-block movement (App. A)
@@ -1195,6 +1197,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     unsigned short* s_gpre = (unsigned short*)(smem_raw + C::off_gpre);
     u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0] total, [1..33] scan tmp
     const int warp = threadIdx.x >> 5;
+    if (ws.ls) nsub = ws.ls->nsub;                  // device-planned round
     const u32 G = gridDim.x;                      // CTAs in the grid
     constexpr u32 MOV = (u32)NW * V;              // movers of one CTA
     // CTAs per subproblem, in proportion to its full blocks; the warps of a
@@ -1265,6 +1268,36 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
 }
 
 // --------------------------------------------------------------- cleanup
+// A bucket whose cleanup is done: buckets up to the base-case capacity go to
+// the list of their base-case size class, sorted in shared memory by the
+// kernels that follow; larger ones recurse (Section 4) as subproblems of the
+// next level, appended to the next-level queue of a device-planned sort or
+// to the chunk's task list of a host-planned one.
+template <class T>
+__device__ __forceinline__ void emit_bucket(const Workspace<T>& ws, Task task, u32 rec_cap) {
+    const u64 size = task.n;
+    if (size > (u64)rec_cap) {
+        if (ws.ls) {
+            const u32 idx = atomicAdd(&ws.ls->next_count, 1u);
+            if (idx < ws.next_cap) ws.ls->next_q[idx] = task;
+            else set_status(ws.ctr, kStatusCapacity);
+        } else {
+            const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
+            if (idx < ws.next_cap) ws.next_tasks[idx] = task;
+            else set_status(ws.ctr, kStatusCapacity);
+        }
+    } else if (size <= (u64)T::kBaseTiny) {
+        const u32 idx = atomicAdd(&ws.ctr->base_tiny, 1u);
+        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_tiny[idx] = task;
+    } else if (size <= (u64)T::kBaseSmall) {
+        const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
+        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
+    } else {
+        const u32 idx = atomicAdd(&ws.ctr->base_large, 1u);
+        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_large[idx] = task;
+    }
+}
+
 // One warp per (subproblem, bucket), taken in ticket order; WPC warps per CTA
 // (subproblems with few stripes: the lower levels).
 template <class T>
@@ -1363,23 +1396,7 @@ __device__ __forceinline__ void cleanup_bucket_warp(typename T::elem_t* arr, con
     const u64 size = Eb - Bb;
     const bool is_eq = sub.eq && (b & 1);
     if (is_eq || size < 2 || lane != 0) return;
-    // buckets up to the base-case capacity are sorted in shared memory by the
-    // base-case kernels that follow; larger ones recurse (Section 4)
-    const Task task{sub.begin + Bb, size};
-    if (size > (u64)rec_cap) {
-        const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
-        if (idx < ws.next_cap) ws.next_tasks[idx] = task;
-        else set_status(ws.ctr, kStatusCapacity);
-    } else if (size <= (u64)T::kBaseTiny) {
-        const u32 idx = atomicAdd(&ws.ctr->base_tiny, 1u);
-        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_tiny[idx] = task;
-    } else if (size <= (u64)T::kBaseSmall) {
-        const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
-        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
-    } else {
-        const u32 idx = atomicAdd(&ws.ctr->base_large, 1u);
-        if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_large[idx] = task;
-    }
+    emit_bucket<T>(ws, Task{sub.begin + Bb, size}, rec_cap);
 }
 
 template <class T>
@@ -1390,16 +1407,26 @@ __global__ void __launch_bounds__(CleanupCfg<T>::TPB)
     typedef CleanupCfg<T> C;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    u32 ticket = 0;
-    if (lane == 0) ticket = atomicAdd(&ws.ctr->ticket, 1u);
-    ticket = __shfl_sync(0xffffffffu, ticket, 0);
-    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
-    // largest bucket count, in increasing bucket order within a subproblem
-    const u32 j = ticket / bstride, b = ticket % bstride;
-    if (j >= nsub) return;
-    if (b == 0 && lane == 0) IPS4O_GUARD(ws.ctr, ws.subs[j].nbuckets <= bstride, ws.subs[j].nbuckets, bstride);
+    if (ws.ls) {                                    // device-planned round: this variant or the CTA one
+        if (ws.ls->cta_cleanup) return;
+        nsub = ws.ls->nsub;
+        bstride = ws.ls->bstride;
+    }
     E* s_ov = (E*)(smem_raw + C::off_ov) + (size_t)warp * C::B;
-    cleanup_bucket_warp<T>(arr, ws, j, b, s_ov, spin_limit, partition_only, rec_cap);
+    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
+    // largest bucket count, in increasing bucket order within a subproblem;
+    // a warp takes its next ticket only after finishing the last, so every
+    // bucket a cleanup waits for is held by a running warp or done
+    for (;;) {
+        u32 ticket = 0;
+        if (lane == 0) ticket = atomicAdd(&ws.ctr->ticket, 1u);
+        ticket = __shfl_sync(0xffffffffu, ticket, 0);
+        const u32 j = ticket / bstride, b = ticket % bstride;
+        if (j >= nsub) return;
+        if (b == 0 && lane == 0) IPS4O_GUARD(ws.ctr, ws.subs[j].nbuckets <= bstride, ws.subs[j].nbuckets, bstride);
+        cleanup_bucket_warp<T>(arr, ws, j, b, s_ov, spin_limit, partition_only, rec_cap);
+        __syncwarp();
+    }
 }
 
 // ------------------------------------------------- cleanup, CTA per bucket
@@ -1416,29 +1443,23 @@ struct CleanupCtaCfg {
     static constexpr size_t smem_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
 };
 
+// Cleanup of bucket b of subproblem j by the whole CTA (CleanupCtaCfg<T>::TPB
+// threads): the same steps as cleanup_bucket_warp, with the partial buffers
+// of many stripes gathered in parallel.
 template <class T>
-__global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
-    k_cleanup_cta(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 bstride, u32 spin_limit, u32 partition_only,
-              u32 rec_cap) {
+__device__ void cleanup_bucket_cta(typename T::elem_t* arr, const Workspace<T>& ws, u32 j, u32 b, u32 bstride,
+                                   u32 spin_limit, u32 partition_only, u32 rec_cap, unsigned char* smem_raw,
+                                   u32* s_ok_p, u32* tmp) {
     typedef typename T::elem_t E;
     typedef CleanupCtaCfg<T> C;
     constexpr int TPB = C::TPB, B = C::B;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     E* s_ov = (E*)(smem_raw + C::off_ov);
     u32* s_lpre = (u32*)(smem_raw + C::off_lpre);
     u64* s_src = (u64*)(smem_raw + C::off_src);
-    __shared__ u32 s_ticket, s_ok;
-    __shared__ u32 tmp[32];
-    if (threadIdx.x == 0) s_ticket = atomicAdd(&ws.ctr->ticket, 1u);
-    __syncthreads();
-    const u32 ticket = s_ticket;
-    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
-    // largest bucket count, in increasing bucket order within a subproblem
-    const u32 j = ticket / bstride, b = ticket % bstride;
-    if (j >= nsub) return;
+    u32& s_ok = *s_ok_p;
     const SubDesc sub = ws.subs[j];
     const u32 nb = sub.nbuckets;
-    if (b == 0) IPS4O_GUARD(ws.ctr, nb <= bstride, nb, bstride);
+    if (b == 0 && threadIdx.x == 0) IPS4O_GUARD(ws.ctr, nb <= bstride, nb, bstride);
     if (b >= nb) return;
     E* A = arr + sub.begin;
     const u64* bstart = ws.bstart + (u64)j * (kMaxBuckets + 1);
@@ -1534,24 +1555,32 @@ __global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
     const u64 size = Eb - Bb;
     const bool is_eq = sub.eq && (b & 1);
     if (is_eq || size < 2) return;
-    if (threadIdx.x == 0) {
-        // buckets up to the base-case capacity are sorted in shared memory by
-        // the base-case kernels that follow; larger ones recurse (Section 4)
-        const Task task{sub.begin + Bb, size};
-        if (size > (u64)rec_cap) {
-            const u32 idx = atomicAdd(&ws.ctr->next_count, 1u);
-            if (idx < ws.next_cap) ws.next_tasks[idx] = task;
-            else set_status(ws.ctr, kStatusCapacity);
-        } else if (size <= (u64)T::kBaseTiny) {
-            const u32 idx = atomicAdd(&ws.ctr->base_tiny, 1u);
-            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_tiny[idx] = task;
-        } else if (size <= (u64)T::kBaseSmall) {
-            const u32 idx = atomicAdd(&ws.ctr->base_small, 1u);
-            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_small[idx] = task;
-        } else {
-            const u32 idx = atomicAdd(&ws.ctr->base_large, 1u);
-            if (IPS4O_GUARD(ws.ctr, idx < ws.max_sub * kMaxBuckets, idx, ws.max_sub)) ws.base_large[idx] = task;
-        }
+    if (threadIdx.x == 0) emit_bucket<T>(ws, Task{sub.begin + Bb, size}, rec_cap);
+}
+
+template <class T>
+__global__ void __launch_bounds__(CleanupCtaCfg<T>::TPB)
+    k_cleanup_cta(typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u32 bstride, u32 spin_limit, u32 partition_only,
+              u32 rec_cap) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ u32 s_ticket, s_ok;
+    __shared__ u32 tmp[32];
+    if (ws.ls) {                                    // device-planned round: this variant or the warp one
+        if (!ws.ls->cta_cleanup) return;
+        nsub = ws.ls->nsub;
+        bstride = ws.ls->bstride;
+    }
+    // tickets enumerate (subproblem, bucket) with bstride >= the chunk's
+    // largest bucket count, in increasing bucket order within a subproblem;
+    // a CTA takes its next ticket only after finishing the last
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) s_ticket = atomicAdd(&ws.ctr->ticket, 1u);
+        __syncthreads();
+        const u32 ticket = s_ticket;
+        const u32 j = ticket / bstride, b = ticket % bstride;
+        if (j >= nsub) return;
+        cleanup_bucket_cta<T>(arr, ws, j, b, bstride, spin_limit, partition_only, rec_cap, smem_raw, &s_ok, tmp);
     }
 }
 

@@ -103,6 +103,7 @@ ips4o_status sort_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s) {
     k_rec_extract<<<grid, 256, 0, s>>>((const u32*)d, n, pairs);
     if ((rc = cuda(cudaGetLastError(), "launch of k_rec_extract")) != IPS4O_OK) return rc;
     rc = sort_pair(st, pairs, n, s, nullptr);
+    if (rc == IPS4O_OK) rc = finalize_pending(st);     // the pair sort is enqueued: wait for it, read its status
     if (rc != IPS4O_OK) return rc;
     const ips4o_stats main_sort = st.stats;
     launches += main_sort.kernel_launches;

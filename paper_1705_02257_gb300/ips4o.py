@@ -161,6 +161,17 @@ def ips4o_stream_status(stream: int = 0) -> int:
     return _lib.ips4o_stream_status(stream)
 
 
+def check(stream: int | None = None) -> None:
+    """Wait for the stream and raise the device-side error of the last
+    enqueue-only sort on it, if any (ips4o_stream_status)."""
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream().cuda_stream
+    rc = ips4o_stream_status(stream)
+    if rc:
+        raise Ips4oError(rc, "ips4o_stream_status")
+
+
 def ips4o_partition(d_ptr: int, n: int, key_type: int, stream: int = 0):
     """Returns (status, bounds, splitters, eq)."""
     bounds = np.zeros(257, dtype=np.uint64)
@@ -256,7 +267,9 @@ def _stream_of(t) -> int:
 
 def sort(t, key_type="u64", stream: int | None = None):
     """Sort a contiguous CUDA tensor in place, viewing its bytes as elements
-    of ``key_type`` ('u64', 'f64', 'pair', 'rec100')."""
+    of ``key_type`` ('u64', 'f64', 'pair', 'rec100').  For u64, f64 and
+    pairs the call only enqueues the work on the stream (device-side errors:
+    ``check(stream)``)."""
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     kt = _kt(key_type)

@@ -75,3 +75,20 @@ def test_class_params_validation(lib):
     assert ips4o.ips4o_set_class_params([(2, 1)]) == 1         # fewer than 4 leaves
     assert ips4o.ips4o_set_class_params([(256, 17)]) == 1      # alpha * leaves > 4096
     assert ips4o.ips4o_get_class_params() == before            # rejected tables change nothing
+
+
+def test_workspace_is_sublinear_in_n(lib):
+    """Theorem 2: the extra space of the sort is O(k b t + log_k(n / n0)).
+    Here t is a fixed number of stripes per SM, so the leftover pool and the
+    per-chunk tables do not grow with n; only the two level queues grow, by
+    n / (base-case size) task entries of 16 bytes each (computed on the host,
+    no GPU needed; 152 SMs when no device is present)."""
+    lib.ips4o_workspace_bytes.restype = ctypes.c_size_t
+    lib.ips4o_workspace_bytes.argtypes = [ctypes.c_size_t, ctypes.c_int]
+    for kt, s, cap in ((0, 8, 16384), (1, 8, 16384), (2, 16, 8192)):
+        w = {k: lib.ips4o_workspace_bytes(1 << k, kt) for k in (24, 26, 28, 30)}
+        for k in (26, 28, 30):
+            queues = 4 * 16 * ((1 << k) - (1 << 24)) // (cap + 1)     # two queues, the fallback list (2x)
+            assert w[k] - w[24] <= queues + 4096, (kt, k, w)
+        # at 2^28 elements: well below 5% of the input
+        assert w[28] < 0.05 * (1 << 28) * s, (kt, w[28])

@@ -203,9 +203,7 @@ def test_stats_counters(ips4o):
     assert st["levels"] >= 1
     assert st["blocks_moved"] > 0
     assert st["base_case_buckets"] > 0
-    assert st["workspace_bytes"] > 0
-    # Theorem 2: the extra space is O(k b t + #subproblems), far below n
-    assert st["workspace_bytes"] < 8 * (1 << 22)
+    assert st["workspace_bytes"] == ips4o.ips4o_workspace_bytes(1 << 22, ips4o.U64)
 
 
 def test_sort_host_roundtrip(ips4o):
@@ -324,3 +322,72 @@ def test_rec100_equal_prefix_tie_break(ips4o):
     hi, lo = _rec_keys(a)
     order = np.lexsort((lo, hi))        # numpy's lexsort is stable
     assert np.array_equal(got, a[order])
+
+
+def test_sort_only_enqueues_and_reports_through_the_stream(ips4o):
+    """ips4o_sort plans the recursion on the device: the call returns while
+    the sort is still running, and the stream status reports its outcome."""
+    a = inputs.u64(1 << 27, "uniform")
+    t = torch.from_numpy(a.view(np.int64).copy()).cuda()
+    s = torch.cuda.current_stream()
+    ips4o.sort(t, "u64")                     # warm-up: the workspace is allocated here
+    torch.cuda.synchronize()
+    t.copy_(torch.from_numpy(a.view(np.int64)))
+    torch.cuda.synchronize()
+    rc = ips4o.ips4o_sort(t.data_ptr(), t.numel(), ips4o.U64, s.cuda_stream)
+    still_running = not s.query()
+    assert rc == 0
+    assert ips4o.ips4o_stream_status(s.cuda_stream) == 0
+    assert still_running
+    out = t.cpu().numpy().view(np.uint64)
+    assert oracle.is_sorted(out, "u64") and oracle.multiset_hash(out, "u64") == oracle.multiset_hash(a, "u64")
+
+
+@pytest.mark.parametrize("kt,n", [("u64", 3_000_017), ("pair", 1_000_003), ("f64", 20_000)])
+def test_sort_captured_in_a_cuda_graph(ips4o, kt, n):
+    """With its workspace reserved, ips4o_sort is capturable: the captured
+    graph, replayed on new contents of the same buffer, sorts them."""
+    kid = ips4o.KEY_TYPES[kt]
+    s = torch.cuda.Stream()
+    a0 = inputs.make(kt, n, "two_dup", seed=3)
+    buf = torch.from_numpy(np.ascontiguousarray(a0).view(np.uint8).reshape(-1).copy()).cuda()
+    with torch.cuda.stream(s):
+        assert ips4o.ips4o_reserve_workspace(n, 1, kid, s.cuda_stream) == 0
+        ips4o.sort(buf, kt, stream=s.cuda_stream)          # first call on the stream: kernel attributes
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        rc = ips4o.ips4o_sort(buf.data_ptr(), n, kid, s.cuda_stream)
+    assert rc == 0
+    for seed in (5, 6):
+        a = inputs.make(kt, n, "uniform" if seed == 5 else "root_dup", seed=seed)
+        buf.copy_(torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)))
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert ips4o.ips4o_stream_status(s.cuda_stream) == 0
+        got = buf.cpu().numpy().view(a.dtype).reshape(a.shape)
+        exp = oracle.sort(a, kt)
+        if kt == "pair":
+            assert np.array_equal(got["key"], exp["key"])
+            assert oracle.multiset_hash(got, kt) == oracle.multiset_hash(a, kt)
+        else:
+            assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+def test_capture_without_reserved_workspace_is_refused(ips4o):
+    """Under capture nothing may be allocated: a sort larger than the
+    stream's workspace returns IPS4O_ERR_TOO_LARGE and queues nothing."""
+    s = torch.cuda.Stream()
+    n = 1 << 22
+    t = torch.zeros(n, dtype=torch.int64, device="cuda")
+    x = torch.zeros(16, dtype=torch.int64, device="cuda")
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        x.add_(1)
+        rc = ips4o.ips4o_sort(t.data_ptr(), n, ips4o.U64, s.cuda_stream)
+    assert rc == 8
+    g.replay()
+    torch.cuda.synchronize()
+    assert int(x.sum().item()) == 16
