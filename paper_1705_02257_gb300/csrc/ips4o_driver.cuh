@@ -122,21 +122,6 @@ u32 fallback_grid(const Caps<T>& c) {
     return c.stack_slots;
 }
 
-// Rounds enqueued for a device-planned sort of n elements: level l has about
-// k^(l-1) subproblems of n / k^(l-1) elements, which take ceil(k^(l-1) /
-// max_sub) rounds, down to the recursion threshold; plus one round for
-// buckets that come out larger than nominal.
-inline u32 rounds_for(u64 n, u64 cap, u32 k_max, u32 max_sub) {
-    double subs = 1.0, m = (double)n;
-    u32 r = 0;
-    while (m > (double)cap && r < 4096) {
-        r += (u32)std::ceil(subs / (double)max_sub);
-        subs *= k_max;
-        m /= k_max;
-    }
-    return r + 1;
-}
-
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Workspace carving: returns total bytes; fills ws when base != nullptr.
@@ -223,6 +208,27 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
     else if (r <= (double)k_max * (double)k_max) k = pow2_ceil_host((u64)std::ceil(std::sqrt(r)));
     else k = k_max;
     return std::min(std::max<u32>(k, 4), k_max);
+}
+
+// Rounds enqueued for a device-planned sort of n elements.  The recursion
+// is followed on nominal sizes: a level of `subs` subproblems of m elements
+// takes ceil(subs / max_sub) rounds and splits each into the number of
+// leaves the planner gives that size (the class table, else leaves_for),
+// down to the recursion threshold.  When the last level's nominal buckets
+// come within a factor of 4 of the threshold, sampling may leave some above
+// it, and one more round is added; rarer stragglers, and any deeper
+// recursion, go to the segment scheduler after the last round.
+inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
+    double subs = 1.0, m = (double)n;
+    u32 r = 0;
+    while (m > (double)cap && r < 4096) {
+        r += (u32)std::ceil(subs / (double)max_sub);
+        const ips4o_class_params cp = class_table()[63 - __builtin_clzll((u64)m)];
+        const u32 K = cp.leaves ? (u32)cp.leaves : leaves_for((u64)m, base_cap, k_max);
+        subs *= K;
+        m /= K;
+    }
+    return r + (m * 4.0 > (double)cap ? 1u : 0u);
 }
 
 #define IPS4O_CUDA(call)                                    \
@@ -651,7 +657,7 @@ struct Driver {
             pa.base_cap = base_cap;
             pa.sms = (u32)st.sms;
             pa.w0 = (u32)std::max(1, prm.stripes_per_sm);
-            const u32 R = rounds_for(n, rc_cap, k_max, c.max_sub);
+            const u32 R = rounds_for(n, rc_cap, base_cap, k_max, c.max_sub);
             const u32 sms = (u32)st.sms;
             for (u32 r = 0; r < R; ++r) {
                 pa.first = r == 0 ? 1u : 0u;
@@ -666,7 +672,7 @@ struct Driver {
                                     d, ws, 0, spin_limit())));
                 IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<2 * sms, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
                                                     stream>>>(d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
-                IPS4O_LAUNCH(5, (k_cleanup<T><<<4 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                IPS4O_LAUNCH(5, (k_cleanup<T><<<8 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
                                     d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
                 IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
                                     d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
