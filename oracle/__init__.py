@@ -7,7 +7,8 @@ sequential samplesort, Sections 3, 4.4 and 4.7 of the paper), compiled with gcc
 on first use; this file only marshals numpy arrays to it.
 
 Key types: 'u64', 'f64', 'pair' (16-byte key/payload), 'rec100' (100-byte
-record, 10-byte key compared as unsigned bytes).
+record, 10-byte key compared as unsigned bytes), 'quartet' (32 bytes: three
+64-bit key words compared lexicographically, one payload word).
 """
 from __future__ import annotations
 
@@ -18,8 +19,8 @@ import threading
 
 import numpy as np
 
-KEY_TYPES = {"u64": 0, "f64": 1, "pair": 2, "rec100": 3}
-ELEM_SIZE = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100}
+KEY_TYPES = {"u64": 0, "f64": 1, "pair": 2, "rec100": 3, "quartet": 4}
+ELEM_SIZE = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "ips4o_oracle.c")
@@ -51,9 +52,9 @@ def _declare(lib):
     lib.oracle_sort.argtypes = [vp, sz, i32, pp]
     lib.oracle_partition.restype = i32
     lib.oracle_partition.argtypes = [vp, sz, i32, pp, vp, vp, ctypes.POINTER(sz),
-                                     ctypes.POINTER(i32), vp, ctypes.POINTER(sz)]
+                                     ctypes.POINTER(i32), vp, ctypes.POINTER(sz), vp]
     lib.oracle_key.restype = None
-    lib.oracle_key.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64)]
+    lib.oracle_key.argtypes = [vp, i32, ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.oracle_rank_counts.restype = i32
     lib.oracle_rank_counts.argtypes = [vp, sz, i32, vp, ctypes.POINTER(u64), ctypes.POINTER(u64)]
     lib.oracle_multiset_hash.restype = i32
@@ -105,11 +106,13 @@ def sort(a: np.ndarray, key_type: str = "u64", lib=None, **params) -> np.ndarray
 
 def partition(a: np.ndarray, key_type: str = "u64", lib=None, **params):
     """One distribution step.  Returns (arranged copy, splitter keys as an
-    (m, 2) uint64 array of (hi, lo), equality flag, bucket bounds)."""
+    (m, 3) uint64 array of (hi, lo, lo2) key words, equality flag, bucket
+    bounds)."""
     out = np.ascontiguousarray(a).copy()
     k = params.get("k", 256)
     hi = np.zeros(k, dtype=np.uint64)
     lo = np.zeros(k, dtype=np.uint64)
+    lo2 = np.zeros(k, dtype=np.uint64)
     bounds = np.zeros(2 * k + 2, dtype=np.uint64)
     m = ctypes.c_size_t(0)
     eq = ctypes.c_int(0)
@@ -117,24 +120,25 @@ def partition(a: np.ndarray, key_type: str = "u64", lib=None, **params):
     rc = (lib or load()).oracle_partition(out.ctypes.data, _count(out, key_type), _kt(key_type),
                                           ctypes.byref(_params(**params)), hi.ctypes.data,
                                           lo.ctypes.data, ctypes.byref(m), ctypes.byref(eq),
-                                          bounds.ctypes.data, ctypes.byref(nb))
+                                          bounds.ctypes.data, ctypes.byref(nb), lo2.ctypes.data)
     if rc != 0:
         raise RuntimeError(f"oracle_partition failed ({rc})")
-    spl = np.stack([hi[: m.value], lo[: m.value]], axis=1)
+    spl = np.stack([hi[: m.value], lo[: m.value], lo2[: m.value]], axis=1)
     return out, spl, bool(eq.value), bounds[: nb.value + 1].astype(np.int64)
 
 
 def keys(a: np.ndarray, key_type: str = "u64") -> np.ndarray:
-    """Comparable keys of every element as an (n, 2) uint64 array (hi, lo)."""
+    """Comparable keys of every element as an (n, 3) uint64 array of key
+    words (hi, lo, lo2), compared lexicographically."""
     lib = load()
     n = _count(a, key_type)
     a = np.ascontiguousarray(a)
     raw = a.view(np.uint8).reshape(n, ELEM_SIZE[key_type]) if n else np.zeros((0, 1), np.uint8)
-    out = np.zeros((n, 2), dtype=np.uint64)
-    h, l_ = ctypes.c_uint64(), ctypes.c_uint64()
+    out = np.zeros((n, 3), dtype=np.uint64)
+    h, l_, l2 = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
     for i in range(n):
-        lib.oracle_key(raw[i].ctypes.data, _kt(key_type), ctypes.byref(h), ctypes.byref(l_))
-        out[i, 0], out[i, 1] = h.value, l_.value
+        lib.oracle_key(raw[i].ctypes.data, _kt(key_type), ctypes.byref(h), ctypes.byref(l_), ctypes.byref(l2))
+        out[i, 0], out[i, 1], out[i, 2] = h.value, l_.value, l2.value
     return out
 
 

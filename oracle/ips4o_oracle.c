@@ -43,13 +43,16 @@
  *   2 pair   16 bytes {u64 key; u64 payload}, ordered by key only.
  *   3 rec100 100 bytes, key = bytes [0,10) compared as unsigned bytes
  *            (lexicographically), payload = bytes [10,100).
+ *   4 quartet 32 bytes {u64 k0, k1, k2; u64 payload}, key = (k0, k1, k2)
+ *            compared lexicographically (Section 5: three key words and one
+ *            word of associated information).
  */
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 #include <math.h>
 
-enum { KT_U64 = 0, KT_F64 = 1, KT_PAIR = 2, KT_REC100 = 3 };
+enum { KT_U64 = 0, KT_F64 = 1, KT_PAIR = 2, KT_REC100 = 3, KT_QUARTET = 4 };
 
 typedef struct {
     int k;          /* maximum number of buckets per level (power of two, >= 2) */
@@ -59,20 +62,21 @@ typedef struct {
     uint64_t seed;  /* sampling seed */
 } oracle_params;
 
-/* Comparable key: (hi, lo) compared lexicographically as unsigned. */
-typedef struct { uint64_t hi, lo; } okey;
+/* Comparable key: (hi, lo, lo2) compared lexicographically as unsigned. */
+typedef struct { uint64_t hi, lo, lo2; } okey;
 
 static size_t elem_size(int kt) {
     switch (kt) {
     case KT_U64: case KT_F64: return 8;
     case KT_PAIR: return 16;
     case KT_REC100: return 100;
+    case KT_QUARTET: return 32;
     }
     return 0;
 }
 
 static okey key_of(const uint8_t* e, int kt) {
-    okey k = {0, 0};
+    okey k = {0, 0, 0};
     uint64_t v;
     switch (kt) {
     case KT_U64:
@@ -88,12 +92,19 @@ static okey key_of(const uint8_t* e, int kt) {
         for (int b = 0; b < 8; ++b) k.hi = (k.hi << 8) | e[b];
         k.lo = ((uint64_t)e[8] << 8) | e[9];
         break;
+    case KT_QUARTET:
+        memcpy(&k.hi, e, 8);
+        memcpy(&k.lo, e + 8, 8);
+        memcpy(&k.lo2, e + 16, 8);
+        break;
     }
     return k;
 }
 
-static int key_less(okey a, okey b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
-static int key_eq(okey a, okey b) { return a.hi == b.hi && a.lo == b.lo; }
+static int key_less(okey a, okey b) {
+    return a.hi < b.hi || (a.hi == b.hi && (a.lo < b.lo || (a.lo == b.lo && a.lo2 < b.lo2)));
+}
+static int key_eq(okey a, okey b) { return a.hi == b.hi && a.lo == b.lo && a.lo2 == b.lo2; }
 
 static int key_cmp_qsort(const void* pa, const void* pb) {
     const okey* a = (const okey*)pa;
@@ -291,14 +302,18 @@ int oracle_sort(void* data, size_t n, int kt, const oracle_params* params) {
  * bounds[0..nb] (caller provides room for 2*k+2 entries), *nb_out. */
 int oracle_partition(void* data, size_t n, int kt, const oracle_params* params,
                      uint64_t* spl_hi, uint64_t* spl_lo, size_t* m_out, int* eq_out,
-                     size_t* bounds, size_t* nb_out) {
+                     size_t* bounds, size_t* nb_out, uint64_t* spl_lo2) {
     size_t s = elem_size(kt);
     if (!s || n < 2 || !data) return -1;
     oracle_params p;
     fill_defaults(&p, params);
     level_result L;
     if (distribute((uint8_t*)data, n, s, kt, &p, 0, 0, &L)) return -1;
-    for (size_t j = 0; j < L.m; ++j) { spl_hi[j] = L.spl[j].hi; spl_lo[j] = L.spl[j].lo; }
+    for (size_t j = 0; j < L.m; ++j) {
+        spl_hi[j] = L.spl[j].hi;
+        spl_lo[j] = L.spl[j].lo;
+        if (spl_lo2) spl_lo2[j] = L.spl[j].lo2;
+    }
     *m_out = L.m;
     *eq_out = L.eq;
     for (size_t b = 0; b <= L.nb; ++b) bounds[b] = L.bounds[b];
@@ -307,10 +322,10 @@ int oracle_partition(void* data, size_t n, int kt, const oracle_params* params,
     return 0;
 }
 
-/* The comparable key of one element, as (hi, lo). */
-void oracle_key(const void* elem, int kt, uint64_t* hi, uint64_t* lo) {
+/* The comparable key of one element, as (hi, lo, lo2). */
+void oracle_key(const void* elem, int kt, uint64_t* hi, uint64_t* lo, uint64_t* lo2) {
     okey k = key_of((const uint8_t*)elem, kt);
-    *hi = k.hi; *lo = k.lo;
+    *hi = k.hi; *lo = k.lo; *lo2 = k.lo2;
 }
 
 /* Order-statistic check at any size: counts the elements of data[0..n)

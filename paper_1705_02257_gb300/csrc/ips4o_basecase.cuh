@@ -99,25 +99,25 @@ struct BaseCfg {
     static constexpr int NW = TPB / 32;
     static constexpr int CAP = CAP_;
     static constexpr int EPT = CAP / TPB;
-    static constexpr int MAXSUB = 2 * CAP;   // sub-buckets of the on-chip distribution: two per element
+    static constexpr int N0 = 1;             // target sub-bucket size
+    static constexpr int MAXSUB = CAP / N0;  // sub-buckets of the on-chip distribution
     static constexpr int LIMIT = 64;         // larger sub-buckets are sorted one at a time by the CTA
     static constexpr int MAXBIG = CAP / LIMIT;
-    // sub-bucket counters (then starts) are 16 bits, two per 32-bit word
-    // (word w: sub-buckets 2w and 2w + 1); word w lives at pad(w) = w + w / 32,
-    // so that the WPT consecutive words each thread scans start in different
-    // banks for the 32 lanes of a warp
-    static constexpr int WORDS = MAXSUB / 2;
-    static constexpr u32 PADDED = WORDS + WORDS / 32 + 1;
+    // sub-bucket counters/starts: entry s at pad(s) = s + s / 32, so that the
+    // SUBS_PER_THREAD consecutive entries each thread scans start in
+    // different banks for the 32 lanes of a warp
+    static constexpr u32 PADDED = MAXSUB + MAXSUB / 32 + 1;
     static constexpr size_t off_data = 0;
     static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[PADDED]
     static constexpr size_t off_tmp = off_off + ((size_t)PADDED * 4 + 15) / 16 * 16;
     static constexpr size_t off_big = off_tmp + 64 * 8;                     // u32[MAXBIG + 1]
     static constexpr size_t smem_bytes = off_big + (MAXBIG + 1) * 4;
-    static constexpr int WPT = WORDS / TPB;
+    static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
-    static_assert(CAP <= 32768 && MAXSUB <= 65536, "starts and sub-bucket indices are packed in 16 bits");
-    static_assert(WORDS % TPB == 0, "whole counter words per thread");
-    __device__ static __forceinline__ u32 pad(u32 w) { return w + (w >> 5); }
+    static_assert(CAP <= 65535, "ranks are packed in 16 bits");
+    static_assert(EPT % 2 == 0, "ranks are packed two per register");
+    static_assert(MAXSUB % TPB == 0, "whole sub-bucket counters per thread");
+    __device__ static __forceinline__ u32 pad(u32 s) { return s + (s >> 5); }
 };
 
 // The three size classes: buckets of at most kBaseTiny elements (the typical
@@ -165,32 +165,28 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 // Sort g[0..m), m <= CAP, with the whole CTA (BaseCfg<T>::TPB threads).
 //
 // The bucket is read once into registers.  Its key range [lo, hi] is split
-// into KB (about 2m) sub-ranges of equal power-of-two width, and every
-// element goes to sub-bucket (key - lo) >> shift; a bucket produced by the
-// sampled distribution steps is close to uniform over its range, so most
-// sub-buckets hold at most one element.  Each element keeps its sub-bucket
-// and its arrival rank in it from the counting pass; after a scan of the
-// counts the elements are scattered into shared memory by sub-bucket, and
-// each element's final position is the start of its sub-bucket plus the
-// number of keys of that sub-bucket that are smaller (or equal and earlier),
-// written there directly.  Sub-buckets of more than LIMIT elements
-// (clustered or repeated keys) are handled afterwards, one at a time by the
-// whole CTA: left as they are when all their keys are equal, else sorted in
-// shared memory by a bitonic network, so the cost stays bounded for any
-// input.
+// into at most KB (about m / N0) sub-ranges of equal power-of-two width, and
+// every element goes to sub-bucket (key - lo) >> shift; a bucket produced by
+// the sampled distribution steps is close to uniform over its range, so the
+// sub-buckets are small.  After a
+// counting-sort scatter into shared memory, each element's final position is
+// the start of its sub-bucket plus the number of keys of that sub-bucket
+// that are smaller (or equal and earlier), and it is written there directly.
+// Sub-buckets of more than LIMIT elements (clustered or repeated keys) are
+// handled afterwards, one at a time by the whole CTA: left as they are when
+// all their keys are equal, else sorted in shared memory by a bitonic
+// network, so the cost stays bounded for any input.
 template <class T, class C>
 __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    constexpr int TPB = C::TPB, EPT = C::EPT, WPT = C::WPT;
+    constexpr int TPB = C::TPB, EPT = C::EPT, SPT = C::SUBS_PER_THREAD;
     if (m < 2) return;
     E* data = (E*)(smem + C::off_data);
-    u32* cw = (u32*)(smem + C::off_off);           // packed sub-bucket counts, then starts
+    u32* off = (u32*)(smem + C::off_off);          // sub-bucket sizes, then (scanned) starts
     u64* tmp = (u64*)(smem + C::off_tmp);
     u32* big_list = (u32*)(smem + C::off_big);     // [0] count, then the large sub-buckets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // start of sub-bucket s (after the scan); s == KB gives m
-    auto start = [&](u32 s) -> u32 { return (cw[C::pad(s >> 1)] >> ((s & 1u) << 4)) & 0xffffu; };
 
     E e[EPT];
     K lo = ~K(0), hi = K(0);
@@ -205,8 +201,8 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         }
     }
 #pragma unroll
-    for (int q = 0; q < WPT; ++q) cw[C::pad(tid * WPT + q)] = 0;
-    if (tid == 0) { cw[C::pad(C::WORDS)] = 0; big_list[0] = 0; }
+    for (int q = 0; q < SPT; ++q) off[C::pad(tid * SPT + q)] = 0;
+    if (tid == 0) { off[C::pad(C::MAXSUB)] = 0; big_list[0] = 0; }
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -226,8 +222,8 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     const bool all_equal = lo == hi;
     __syncthreads();                               // every thread has read tmp before it is reused
     if (all_equal) return;                         // all keys equal: already sorted (uniform exit)
-    u32 KB = pow2_ceil_u32(2 * m);
-    KB = KB > (u32)C::MAXSUB ? (u32)C::MAXSUB : KB;
+    u32 KB = pow2_ceil_u32((m + C::N0 - 1) / C::N0);
+    KB = KB < 2 ? 2 : (KB > (u32)C::MAXSUB ? (u32)C::MAXSUB : KB);
     // sub-bucket = (key - lo) >> shift, with shift chosen so that the whole
     // range [lo, hi] maps into [0, KB): a monotone map of the key, so lower
     // sub-buckets hold smaller keys; sub-buckets cover equal key ranges
@@ -239,48 +235,46 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         const u64 d = (u64)(k - lo) >> shift;
         return d < (u64)KB ? (u32)d : KB - 1;
     };
-    // sub-bucket << 16 | arrival rank in it, per element
-    u32 sr[EPT];
+    u32 rk2[EPT / 2];
+#pragma unroll
+    for (int q = 0; q < EPT / 2; ++q) rk2[q] = 0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
-        sr[q] = 0;
         if (idx < m) {
-            const u32 sb = sub_of(T::key(e[q]));
-            const u32 sh = (sb & 1u) << 4;
-            const u32 old = atomicAdd(&cw[C::pad(sb >> 1)], 1u << sh);
-            sr[q] = (sb << 16) | ((old >> sh) & 0xffffu);
+            const u32 r = atomicAdd(&off[C::pad(sub_of(T::key(e[q])))], 1u);
+            rk2[q / 2] |= r << (16 * (q & 1));
         }
     }
     __syncthreads();
-    // exclusive scan of the sub-bucket sizes in place (WPT consecutive words,
-    // two counts each, per thread, read twice rather than held in
-    // registers); the word after the last receives the total
+    // exclusive scan of the sub-bucket sizes in place (SPT consecutive entries
+    // per thread, read twice rather than held in registers); entry MAXSUB
+    // receives the total
     u32 csum = 0;
 #pragma unroll
-    for (int q = 0; q < WPT; ++q) {
-        const u32 w = cw[C::pad(tid * WPT + q)];
-        const u32 c0 = w & 0xffffu, c1 = w >> 16;
-        csum += c0 + c1;
-        if (c0 > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = 2 * (tid * WPT + q);
-        if (c1 > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = 2 * (tid * WPT + q) + 1;
+    for (int q = 0; q < SPT; ++q) {
+        const u32 cq = off[C::pad(tid * SPT + q)];
+        csum += cq;
+        if (cq > (u32)C::LIMIT) big_list[1 + atomicAdd(&big_list[0], 1u)] = tid * SPT + q;
     }
     __syncthreads();
     u32 tot;
     u32 pre = block_exclusive_scan<u32>(csum, (u32*)tmp, &tot);
 #pragma unroll
-    for (int q = 0; q < WPT; ++q) {
-        const u32 w = cw[C::pad(tid * WPT + q)];
-        const u32 c0 = w & 0xffffu, c1 = w >> 16;
-        cw[C::pad(tid * WPT + q)] = pre | ((pre + c0) << 16);
-        pre += c0 + c1;
+    for (int q = 0; q < SPT; ++q) {
+        const u32 cq = off[C::pad(tid * SPT + q)];
+        off[C::pad(tid * SPT + q)] = pre;
+        pre += cq;
     }
-    if (tid == TPB - 1) cw[C::pad(C::WORDS)] = pre;
+    if (tid == TPB - 1) off[C::pad(C::MAXSUB)] = pre;
     __syncthreads();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
-        if (idx < m) data[start(sr[q] >> 16) + (sr[q] & 0xffffu)] = e[q];
+        if (idx < m) {
+            const u32 r = (rk2[q / 2] >> (16 * (q & 1))) & 0xffffu;
+            data[off[C::pad(sub_of(T::key(e[q])))] + r] = e[q];
+        }
     }
     __syncthreads();
     // final position = sub-bucket start + rank of the key within it
@@ -292,7 +286,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
             const E x = data[i];
             const K k = T::key(x);
             const u32 sb = sub_of(k);
-            const u32 o = start(sb), o1 = start(sb + 1);
+            const u32 o = off[C::pad(sb)], o1 = off[C::pad(sb + 1)];
             if (o1 - o > (u32)C::LIMIT) continue;
             u32 r = 0;
             for (u32 jj = o; jj < o1; ++jj) {
@@ -305,7 +299,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     const u32 nbig = big_list[0];
     for (u32 q = 0; q < nbig; ++q) {
         const u32 sb = big_list[1 + q];
-        const u32 o = start(sb), len = start(sb + 1) - o;
+        const u32 o = off[C::pad(sb)], len = off[C::pad(sb + 1)] - o;
         // all keys equal: any order is sorted
         const K k0 = T::key(data[o]);
         int differs = 0;

@@ -26,8 +26,8 @@ constexpr int kDefaultAlpha = 16;
 // SM are held at once (the leftover pool, Theorem 2's O(k b t) with t a
 // multiple of the SM count, independent of n), and at most this many
 // subproblems form one round's chunk.
-constexpr u64 kRoundStripesPerSm = 4;
-constexpr u32 kRoundMaxSub = 512;
+constexpr u64 kRoundStripesPerSm = 2;
+constexpr u32 kRoundMaxSub = 1024;
 
 inline u32 pow2_ceil_host(u64 x) {
     u32 p = 1;
@@ -216,8 +216,9 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
 // leaves the planner gives that size (the class table, else leaves_for),
 // down to the recursion threshold.  When the last level's nominal buckets
 // come within a factor of 4 of the threshold, sampling may leave some above
-// it, and one more round is added; rarer stragglers, and any deeper
-// recursion, go to the segment scheduler after the last round.
+// it, and one more round is added; one more round again takes a level with
+// more subproblems than nominal (skewed keys).  Rarer stragglers, and any
+// deeper recursion, go to the segment scheduler after the last round.
 inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
     double subs = 1.0, m = (double)n;
     u32 r = 0;
@@ -228,7 +229,7 @@ inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
         subs *= K;
         m /= K;
     }
-    return r + (m * 4.0 > (double)cap ? 1u : 0u);
+    return r + 1 + (m * 4.0 > (double)cap ? 1u : 0u);
 }
 
 #define IPS4O_CUDA(call)                                    \

@@ -28,10 +28,12 @@ DISTRIBUTIONS = (
 _DIST_ID = {name: i for i, name in enumerate(DISTRIBUTIONS)}
 
 # Seeds: 1 input values, 2 AlmostSorted swaps, 3 payloads, 4 batch lengths,
-# 5 arrival times.
+# 5 arrival times, 6 and 7 the second and third key words of quartets.
 SEED_VALUES, SEED_SWAPS, SEED_PAYLOAD, SEED_LENGTHS, SEED_ARRIVALS = 1, 2, 3, 4, 5
+SEED_QUARTET_K1, SEED_QUARTET_K2 = 6, 7
 
 PAIR_DTYPE = np.dtype([("key", "<u8"), ("payload", "<u8")])
+QUARTET_DTYPE = np.dtype([("k0", "<u8"), ("k1", "<u8"), ("k2", "<u8"), ("payload", "<u8")])
 REC100_DTYPE = np.dtype((np.void, 100))
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -176,8 +178,22 @@ def request_stream(count: int, lo_log2: float = 10, hi_log2: float = 26, rate: f
     return sizes, types, dists, np.cumsum(gaps)
 
 
+def quartet(n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:
+    """n quartets (Section 5: three key words and one word of associated
+    information).  The first key word follows the distribution; the second
+    takes four values (SplitMix64 stream 6 mod 4), so that elements with equal
+    first words are ordered by the later words; the third and the payload are
+    the SplitMix64 streams 7 and 3."""
+    out = np.empty(n, dtype=QUARTET_DTYPE)
+    out["k0"] = u64(n, dist, seed)
+    out["k1"] = splitmix64_range(n, SEED_QUARTET_K1) % np.uint64(4)
+    out["k2"] = splitmix64_range(n, SEED_QUARTET_K2)
+    out["payload"] = splitmix64_range(n, SEED_PAYLOAD)
+    return out
+
+
 def make(key_type: str, n: int, dist: str = "uniform", seed: int = SEED_VALUES) -> np.ndarray:
-    """Inputs by key-type name: 'u64', 'f64', 'pair' or 'rec100'."""
+    """Inputs by key-type name: 'u64', 'f64', 'pair', 'rec100' or 'quartet'."""
     if key_type == "u64":
         return u64(n, dist, seed)
     if key_type == "f64":
@@ -186,4 +202,6 @@ def make(key_type: str, n: int, dist: str = "uniform", seed: int = SEED_VALUES) 
         return pair(n, dist, seed)
     if key_type == "rec100":
         return rec100(n, dist, seed)
+    if key_type == "quartet":
+        return quartet(n, dist, seed)
     raise ValueError(f"unknown key type {key_type!r}")

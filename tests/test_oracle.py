@@ -116,7 +116,7 @@ def _check_partition(a, key_type="u64", **params):
     assert bounds[0] == 0 and bounds[-1] == n
     assert np.all(np.diff(bounds) >= 0)
     keys = oracle.keys(out, key_type) if key_type != "u64" else np.stack(
-        [out, np.zeros_like(out)], axis=1)
+        [out, np.zeros_like(out), np.zeros_like(out)], axis=1)
     s_hi = spl[:, 0]
     assert np.all(np.diff(s_hi.astype(np.float64)) >= 0)
     nb = len(bounds) - 1
@@ -176,7 +176,7 @@ def test_partition_duplicates_turn_on_equality_buckets():
     assert not eq2
 
 
-@pytest.mark.parametrize("key_type", ["f64", "pair", "rec100"])
+@pytest.mark.parametrize("key_type", ["f64", "pair", "rec100", "quartet"])
 def test_partition_other_types(key_type):
     a = inputs.make(key_type, 3000, "uniform")
     _check_partition(a, key_type)
@@ -248,3 +248,27 @@ def test_splitters_are_equally_spaced_order_statistics():
     expected = np.arange(1, k) / k
     assert np.all(np.abs(means - expected) < 0.025), means
     assert abs(float(np.mean(means - expected))) < 0.012, means
+
+
+# ---------------------------------------------------------------- quartets
+@pytest.mark.parametrize("dist", DISTS)
+def test_quartet_matches_numpy_lexsort(dist):
+    # Section 5: Quartet elements are compared lexicographically on their
+    # three key words; numpy's lexsort (last key primary) gives the unique
+    # key sequence, and the payloads form the same multiset
+    a = inputs.quartet(20_011, dist)
+    out = oracle.sort(a, "quartet")
+    exp = a[np.lexsort((a["k2"], a["k1"], a["k0"]))]
+    for f in ("k0", "k1", "k2"):
+        assert np.array_equal(out[f], exp[f])
+    assert np.array_equal(np.sort(out, order=["k0", "k1", "k2", "payload"]),
+                          np.sort(a, order=["k0", "k1", "k2", "payload"]))
+
+
+def test_quartet_ties_decided_by_later_words():
+    # equal first words (Ones): the order comes from k1, then k2 alone
+    a = inputs.quartet(5000, "ones")
+    out = oracle.sort(a, "quartet", k=8, n0=4)
+    assert np.all(out["k0"] == 1)
+    pairs = list(zip(out["k1"].tolist(), out["k2"].tolist()))
+    assert pairs == sorted(pairs)

@@ -41,6 +41,9 @@ MUTANTS = {
     # splitters taken one place off the equal spacing of Section 3
     "splitter_spacing": ("okey c = sample[(size_t)j * alpha - 1];",
                          "okey c = sample[(size_t)j * alpha - (j < k - 1 ? 0 : 1)];"),
+    # the third key word of a quartet ignored in comparisons (Section 5)
+    "quartet_third_word": ("return a.hi < b.hi || (a.hi == b.hi && (a.lo < b.lo || (a.lo == b.lo && a.lo2 < b.lo2)));",
+                           "return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);"),
     # range buckets skipped instead of equality buckets during recursion
     "recurse_skip": ("if (L.eq && (b % 2 == 1)) continue;",
                      "if (L.eq && (b % 2 == 0)) continue;"),
