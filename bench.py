@@ -43,10 +43,12 @@ METRIC = "keys/s"
 # capture when one of these kernels changes.
 NOMINAL_HBM_GBS = 7900.0      # the data-sheet HBM3e bandwidth, for context beside the measured peak
 TRAFFIC_2P28_U64_UNIFORM = {"classify": 4.045e9, "block_permutation": 3.944e9, "base_case": 3.808e9}
-ELEM_BYTES = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100}
-DTYPE_NAME = {"u64": "u64", "f64": "f64", "pair": "u64 key + u64 payload", "rec100": "80-bit byte key + 90-byte payload"}
+ELEM_BYTES = {"u64": 8, "f64": 8, "pair": 16, "rec100": 100, "quartet": 32}
+DTYPE_NAME = {"u64": "u64", "f64": "f64", "pair": "u64 key + u64 payload", "rec100": "80-bit byte key + 90-byte payload",
+              "quartet": "3 x u64 key + u64 payload"}
 KT_LABEL = {"u64": "uint64 keys", "f64": "float64 keys", "pair": "16-byte (uint64 key, uint64 payload) pairs",
-            "rec100": "100-byte records (10-byte key)"}
+            "rec100": "100-byte records (10-byte key)",
+            "quartet": "32-byte quartets (three uint64 key words, one payload word)"}
 
 
 def _sorted_keys(t, kt) -> bool:
@@ -61,6 +63,11 @@ def _sorted_keys(t, kt) -> bool:
         lo = (b[:, 7] << 16) | (b[:, 8] << 8) | b[:, 9]
         d_hi = hi[1:] - hi[:-1]
         ok = (d_hi > 0) | ((d_hi == 0) & (lo[1:] >= lo[:-1]))
+        return bool(ok.all().item())
+    if kt == "quartet":
+        k = t.view(torch.int64).view(-1, 4)[:, :3] ^ (-(1 << 63))
+        a, b = k[:-1], k[1:]
+        ok = (a[:, 0] < b[:, 0]) | ((a[:, 0] == b[:, 0]) & ((a[:, 1] < b[:, 1]) | ((a[:, 1] == b[:, 1]) & (a[:, 2] <= b[:, 2]))))
         return bool(ok.all().item())
     if kt == "f64":
         x = t.view(torch.float64)
@@ -718,7 +725,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--dist", default="uniform")
     ap.add_argument("--log2n", type=int, default=LOG2N)
-    ap.add_argument("--key-type", default="u64", choices=["u64", "f64", "pair", "rec100"],
+    ap.add_argument("--key-type", default="u64", choices=["u64", "f64", "pair", "rec100", "quartet"],
                     help="plain workload: element type (f64 and pair at 2^27, rec100 at 2^24 in the paper's table)")
     ap.add_argument("--ref-log2n", type=int, default=22)
     ap.add_argument("--cpu-log2n", type=int, default=24)

@@ -53,13 +53,18 @@ typedef enum {
                               ordered as (b has sign) ? ~b : b | 2^63, a total order that
                               equals '<' on non-NaN values and puts -0.0 before +0.0 */
     IPS4O_PAIR_U64 = 2,    /* 16-byte {uint64 key; uint64 payload}, ordered by key; 16-byte aligned */
-    IPS4O_REC100_K10 = 3   /* 100-byte record, key = bytes [0,10) compared as unsigned bytes
+    IPS4O_REC100_K10 = 3,  /* 100-byte record, key = bytes [0,10) compared as unsigned bytes
                               (lexicographic), payload = bytes [10,100); 4-byte aligned.
                               Sorted through 16-byte (key prefix, index) pairs and one gather
                               of the records: NOT in place, it needs 132 bytes of extra device
                               memory per record (see ips4o_workspace_bytes); records with equal
                               keys keep their input order.  ips4o_sort and ips4o_sort_host
                               only; the other entry points return IPS4O_ERR_UNSUPPORTED_TYPE. */
+    IPS4O_QUARTET_U64 = 4  /* 32-byte quartet {uint64 k0, k1, k2; uint64 payload} (Section 5's
+                              Quartet: three key words and one word of associated information),
+                              ordered by (k0, k1, k2) lexicographically; 16-byte aligned; sorted
+                              in place.  ips4o_partition reports the splitters' k0 words.  Not
+                              supported by ips4o_sort_noalloc. */
 } ips4o_key_type;
 
 typedef enum {

@@ -204,14 +204,17 @@ static size_t elem_size(int kt) {
     case IPS4O_F64: return 8;
     case IPS4O_PAIR_U64: return 16;
     case IPS4O_REC100_K10: return 100;
+    case IPS4O_QUARTET_U64: return 32;
     default: return 0;
     }
 }
 
-static size_t elem_align(int kt) { return kt == IPS4O_REC100_K10 ? 4 : elem_size(kt); }
+static size_t elem_align(int kt) {
+    return kt == IPS4O_REC100_K10 ? 4 : (kt == IPS4O_QUARTET_U64 ? 16 : elem_size(kt));
+}
 
 static ips4o_status check_args(const void* p, size_t n, int kt) {
-    if (kt < 0 || kt > IPS4O_REC100_K10) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (kt < 0 || kt > IPS4O_QUARTET_U64) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (elem_size(kt) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (n > 1 && !p) return IPS4O_ERR_INVALID_ARG;
     // one bucket region of the block permutation holds at most 2^25 - 2^16 - 2
@@ -227,6 +230,7 @@ static ips4o_status dispatch(DeviceState& st, void* d, size_t n, int kt, cudaStr
     case IPS4O_U64: rc = sort_u64(st, d, n, s, part); break;
     case IPS4O_F64: rc = sort_f64(st, d, n, s, part); break;
     case IPS4O_PAIR_U64: rc = sort_pair(st, d, n, s, part); break;
+    case IPS4O_QUARTET_U64: rc = sort_quartet(st, d, n, s, part); break;
     case IPS4O_REC100_K10:
         if (part) return IPS4O_ERR_UNSUPPORTED_TYPE;   // records are sorted through key + index pairs
         rc = sort_rec100(st, d, n, s);
@@ -244,6 +248,7 @@ static ips4o_status dispatch_segments(DeviceState& st, void* d, const std::vecto
     case IPS4O_U64: rc = sort_segments_u64(st, d, segs, s); break;
     case IPS4O_F64: rc = sort_segments_f64(st, d, segs, s); break;
     case IPS4O_PAIR_U64: rc = sort_segments_pair(st, d, segs, s); break;
+    case IPS4O_QUARTET_U64: rc = sort_segments_quartet(st, d, segs, s); break;
     default: return IPS4O_ERR_UNSUPPORTED_TYPE;
     }
     publish_stats(st);
@@ -293,7 +298,7 @@ ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream) {
 
 ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t num_segments, int key_type,
                                   void* stream) {
-    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (key_type < 0 || key_type > IPS4O_QUARTET_U64 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (num_segments == 0) return IPS4O_OK;
     if (!offsets) return IPS4O_ERR_INVALID_ARG;
     if (d_base && ((uintptr_t)d_base % elem_size(key_type)) != 0) return IPS4O_ERR_MISALIGNED;
@@ -317,7 +322,7 @@ ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t 
 
 ips4o_status ips4o_sort_segmented_async(void* d_base, const uint64_t* d_offsets, size_t num_segments, int key_type,
                                         void* stream) {
-    if (key_type < 0 || key_type > IPS4O_PAIR_U64) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (key_type < 0 || key_type > IPS4O_QUARTET_U64 || key_type == IPS4O_REC100_K10) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (num_segments == 0) return IPS4O_OK;
     if (!d_offsets || !d_base) return IPS4O_ERR_INVALID_ARG;
     if (((uintptr_t)d_base % elem_align(key_type)) != 0) return IPS4O_ERR_MISALIGNED;
@@ -330,12 +335,13 @@ ips4o_status ips4o_sort_segmented_async(void* d_base, const uint64_t* d_offsets,
     switch (key_type) {
     case IPS4O_U64: return enqueue_segments_u64(*st, d_base, d_offsets, num_segments, s);
     case IPS4O_F64: return enqueue_segments_f64(*st, d_base, d_offsets, num_segments, s);
+    case IPS4O_QUARTET_U64: return enqueue_segments_quartet(*st, d_base, d_offsets, num_segments, s);
     default: return enqueue_segments_pair(*st, d_base, d_offsets, num_segments, s);
     }
 }
 
 ips4o_status ips4o_sort_batched(void* const* ptrs, const uint64_t* lens, size_t count, int key_type, void* stream) {
-    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (key_type < 0 || key_type > IPS4O_QUARTET_U64 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     if (count == 0) return IPS4O_OK;
     if (!ptrs || !lens) return IPS4O_ERR_INVALID_ARG;
     const size_t es = elem_size(key_type);
@@ -395,6 +401,7 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
         switch (key_type) {
         case IPS4O_U64: rc = sort_from_u64(*st, st->d_host_copy, h_dev, n, s); break;
         case IPS4O_F64: rc = sort_from_f64(*st, st->d_host_copy, h_dev, n, s); break;
+        case IPS4O_QUARTET_U64: rc = sort_from_quartet(*st, st->d_host_copy, h_dev, n, s); break;
         default: rc = sort_from_pair(*st, st->d_host_copy, h_dev, n, s); break;
         }
         publish_stats(*st);
@@ -445,13 +452,14 @@ size_t ips4o_workspace_bytes(size_t n, int key_type) {
     case IPS4O_U64: return workspace_bytes_u64(n, sms);
     case IPS4O_F64: return workspace_bytes_f64(n, sms);
     case IPS4O_PAIR_U64: return workspace_bytes_pair(n, sms);
+    case IPS4O_QUARTET_U64: return workspace_bytes_quartet(n, sms);
     case IPS4O_REC100_K10: return workspace_bytes_pair(n, sms) + rec100_aux_bytes(n);
     default: return 0;
     }
 }
 
 ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type, void* stream) {
-    if (key_type < 0 || key_type > IPS4O_REC100_K10 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
+    if (key_type < 0 || key_type > IPS4O_QUARTET_U64 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;
     cudaError_t e;
     DeviceState* st = stream_state(stream, &e);
     if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
@@ -460,6 +468,7 @@ ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type
     case IPS4O_U64: return reserve_u64(*st, n, num_segments);
     case IPS4O_F64: return reserve_f64(*st, n, num_segments);
     case IPS4O_PAIR_U64: return reserve_pair(*st, n, num_segments);
+    case IPS4O_QUARTET_U64: return reserve_quartet(*st, n, num_segments);
     default: {
         ips4o_status rc = reserve_pair(*st, n, num_segments);
         return rc != IPS4O_OK ? rc : ensure_device_buffer(&st->d_aux, &st->aux_bytes, rec100_aux_bytes(n));
@@ -522,6 +531,7 @@ ips4o_status ips4o_set_class_params(const ips4o_class_params* table, size_t coun
     ips4o_status rc = upload_class_table_u64(t);
     if (rc == IPS4O_OK) rc = upload_class_table_f64(t);
     if (rc == IPS4O_OK) rc = upload_class_table_pair(t);
+    if (rc == IPS4O_OK) rc = upload_class_table_quartet(t);
     return rc;
 }
 
@@ -565,6 +575,7 @@ size_t ips4o_base_case_capacity(int key_type) {
     case IPS4O_U64: return TU64::kBaseCap;
     case IPS4O_F64: return TF64::kBaseCap;
     case IPS4O_PAIR_U64: return TPair::kBaseCap;
+    case IPS4O_QUARTET_U64: return TQuartet::kBaseCap;
     default: return 0;
     }
 }

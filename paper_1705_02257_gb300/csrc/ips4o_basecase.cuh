@@ -23,6 +23,14 @@ template <class K>
 __device__ __forceinline__ K key_max();
 template <>
 __device__ __forceinline__ u64 key_max<u64>() { return ~0ull; }
+template <>
+__device__ __forceinline__ QKey key_max<QKey>() { return QKey{~0ull, ~0ull, ~0ull}; }
+template <class K>
+__device__ __forceinline__ K key_min();
+template <>
+__device__ __forceinline__ u64 key_min<u64>() { return 0ull; }
+template <>
+__device__ __forceinline__ QKey key_min<QKey>() { return QKey{0ull, 0ull, 0ull}; }
 
 __device__ __forceinline__ u32 pow2_ceil_u32(u32 x) {
     return x <= 1 ? 1u : (1u << (32 - __clz(x - 1)));
@@ -69,7 +77,7 @@ __device__ void select_splitters(const K* keys, u32 kk, u32 alpha, K* cand, u32*
         __syncthreads();
     }
     const u32 keep = (threadIdx.x < ncand && (threadIdx.x == 0 || cand[threadIdx.x] != cand[threadIdx.x - 1])) ? 1u : 0u;
-    const K mine = threadIdx.x < ncand ? cand[threadIdx.x] : K(0);
+    const K mine = threadIdx.x < ncand ? cand[threadIdx.x] : key_min<K>();
     u32 m;
     const u32 pos = block_exclusive_scan<u32>(keep, scan_tmp, &m);
     __syncthreads();
@@ -110,7 +118,7 @@ struct BaseCfg {
     static constexpr size_t off_data = 0;
     static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[PADDED]
     static constexpr size_t off_tmp = off_off + ((size_t)PADDED * 4 + 15) / 16 * 16;
-    static constexpr size_t off_big = off_tmp + 64 * 8;                     // u32[MAXBIG + 1]
+    static constexpr size_t off_big = off_tmp + 64 * sizeof(K);             // u32[MAXBIG + 1]
     static constexpr size_t smem_bytes = off_big + (MAXBIG + 1) * 4;
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
@@ -184,12 +192,12 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     if (m < 2) return;
     E* data = (E*)(smem + C::off_data);
     u32* off = (u32*)(smem + C::off_off);          // sub-bucket sizes, then (scanned) starts
-    u64* tmp = (u64*)(smem + C::off_tmp);
+    K* tmp = (K*)(smem + C::off_tmp);
     u32* big_list = (u32*)(smem + C::off_big);     // [0] count, then the large sub-buckets
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     E e[EPT];
-    K lo = ~K(0), hi = K(0);
+    K lo = key_max<K>(), hi = key_min<K>();
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;
@@ -206,7 +214,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     // key range of the bucket
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const K a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+        const K a = shfl_xor_key(lo, o), b = shfl_xor_key(hi, o);
         lo = a < lo ? a : lo;
         hi = b > hi ? b : hi;
     }
@@ -227,12 +235,16 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     // sub-bucket = (key - lo) >> shift, with shift chosen so that the whole
     // range [lo, hi] maps into [0, KB): a monotone map of the key, so lower
     // sub-buckets hold smaller keys; sub-buckets cover equal key ranges
-    const u64 range = (u64)(hi - lo);             // >= 1
-    const int bits = 64 - __clzll((long long)range);
+    // (for a key of several words, the sub-buckets split the range of the
+    // leading word; keys equal in it and different in later words share a
+    // sub-bucket, which the rank loop or the bitonic network then orders)
+    const u64 lo_w = T::sub_key(lo);
+    const u64 range = T::sub_key(hi) - lo_w;      // >= 1 for one-word keys
+    const int bits = range ? 64 - __clzll((long long)range) : 0;
     const int logkb = 31 - __clz(KB);
     const int shift = bits > logkb ? bits - logkb : 0;
     auto sub_of = [&](const K& k) -> u32 {
-        const u64 d = (u64)(k - lo) >> shift;
+        const u64 d = (T::sub_key(k) - lo_w) >> shift;
         return d < (u64)KB ? (u32)d : KB - 1;
     };
     u32 rk2[EPT / 2];

@@ -54,9 +54,11 @@ struct TU64 {
     static constexpr int kBaseTiny = 4096;             // base case size class sorted by 256-thread CTAs
     static constexpr int kBaseSmall = 8192;            // base case size class sorted by 512-thread CTAs
     static constexpr int kBaseCap = 16384;             // largest bucket sorted in shared memory (128 KiB)
+    static constexpr int kSampleMax = 4096;            // largest sample (alpha * leaves) of a step
     __host__ __device__ static inline key_t key(const elem_t& e) { return e; }
     __host__ __device__ static inline elem_t unkey(const key_t& k) { return k; }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+    __host__ __device__ static inline u64 sub_key(const key_t& k) { return k; }   // the key's leading word
 };
 
 struct TF64 {
@@ -67,6 +69,7 @@ struct TF64 {
     static constexpr int kBaseTiny = 4096;
     static constexpr int kBaseSmall = 8192;
     static constexpr int kBaseCap = 16384;
+    static constexpr int kSampleMax = 4096;
     __host__ __device__ static inline key_t key(const elem_t& e) {
         return (e >> 63) ? ~e : (e | 0x8000000000000000ull);
     }
@@ -74,6 +77,7 @@ struct TF64 {
         return (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
     }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+    __host__ __device__ static inline u64 sub_key(const key_t& k) { return k; }
 };
 
 struct alignas(16) PairElem {
@@ -89,9 +93,53 @@ struct TPair {
     static constexpr int kBaseTiny = 2048;
     static constexpr int kBaseSmall = 4096;
     static constexpr int kBaseCap = 8192;
+    static constexpr int kSampleMax = 4096;
     __host__ __device__ static inline key_t key(const elem_t& e) { return e.k; }
     __host__ __device__ static inline u64 key_bits(const key_t& k) { return k; }
+    __host__ __device__ static inline u64 sub_key(const key_t& k) { return k; }
 };
+
+// Quartet (Section 5: three key words and one word of associated
+// information, compared lexicographically): 32 bytes, key (k0, k1, k2).
+struct QKey {
+    u64 a, b, c;
+};
+__host__ __device__ __forceinline__ bool operator<(const QKey& x, const QKey& y) {
+    return x.a < y.a || (x.a == y.a && (x.b < y.b || (x.b == y.b && x.c < y.c)));
+}
+__host__ __device__ __forceinline__ bool operator==(const QKey& x, const QKey& y) {
+    return x.a == y.a && x.b == y.b && x.c == y.c;
+}
+__host__ __device__ __forceinline__ bool operator!=(const QKey& x, const QKey& y) { return !(x == y); }
+__host__ __device__ __forceinline__ bool operator>(const QKey& x, const QKey& y) { return y < x; }
+__host__ __device__ __forceinline__ bool operator<=(const QKey& x, const QKey& y) { return !(y < x); }
+__host__ __device__ __forceinline__ bool operator>=(const QKey& x, const QKey& y) { return !(x < y); }
+
+struct alignas(16) QuartetElem {
+    u64 k0, k1, k2;
+    u64 p;
+};
+
+struct TQuartet {
+    typedef QuartetElem elem_t;
+    typedef QKey key_t;
+    static constexpr int kId = 3;
+    static constexpr int kBlock = 16;                 // 16 x 32 B = 512 B
+    static constexpr int kBaseTiny = 1024;
+    static constexpr int kBaseSmall = 2048;
+    static constexpr int kBaseCap = 4096;              // 128 KiB of shared memory
+    static constexpr int kSampleMax = 1024;            // 24 KiB of keys
+    __host__ __device__ static inline key_t key(const elem_t& e) { return QKey{e.k0, e.k1, e.k2}; }
+    __host__ __device__ static inline u64 key_bits(const key_t& k) { return k.a; }
+    __host__ __device__ static inline u64 sub_key(const key_t& k) { return k.a; }
+};
+
+// Warp shuffle of a key of any of the types above.
+__device__ __forceinline__ u64 shfl_xor_key(u64 v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ QKey shfl_xor_key(const QKey& v, int o) {
+    return QKey{__shfl_xor_sync(0xffffffffu, v.a, o), __shfl_xor_sync(0xffffffffu, v.b, o),
+                __shfl_xor_sync(0xffffffffu, v.c, o)};
+}
 
 // ------------------------------------------------------------ descriptors
 // One subproblem (a bucket of the previous level, or the whole input) of a
@@ -228,6 +276,11 @@ template <>
 __device__ __forceinline__ void cp_async<16>(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
                  : "memory");
+}
+template <>
+__device__ __forceinline__ void cp_async<32>(void* smem, const void* gmem) {
+    cp_async<16>(smem, gmem);
+    cp_async<16>((char*)smem + 16, (const char*)gmem + 16);
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>

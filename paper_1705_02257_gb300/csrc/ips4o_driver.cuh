@@ -495,7 +495,7 @@ struct Driver {
             u32 K = partition ? k_max : (cp.leaves ? (u32)cp.leaves : leaves_for(t.n, base_cap, k_max));
             u32 alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
             if (!partition && cp.alpha) alpha = cp.alpha;
-            alpha = std::max<u32>(1, std::min<u32>(alpha, 4096 / K));
+            alpha = std::max<u32>(1, std::min<u32>(alpha, (u32)T::kSampleMax / K));
             u64 ns = std::max<u64>(1, (t.n + stripe_len - 1) / stripe_len);
             ns = std::min<u64>(ns, kMaxStripesPerSub);
             u64 slen, need;

@@ -100,6 +100,14 @@ ips4o_status sort_noalloc_pair(DeviceState& st, void* d, size_t n, cudaStream_t 
 ips4o_status reserve_u64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments);
+ips4o_status sort_quartet(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
+ips4o_status sort_from_quartet(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s);
+ips4o_status sort_segments_quartet(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
+ips4o_status enqueue_segments_quartet(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count,
+                                      cudaStream_t s);
+ips4o_status upload_class_table_quartet(const ips4o_class_params* t);
+ips4o_status reserve_quartet(DeviceState& st, size_t n, size_t num_segments);
+size_t workspace_bytes_quartet(size_t n, int sms);
 ips4o_status sort_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s);
 size_t rec100_aux_bytes(size_t n);
 size_t workspace_bytes_u64(size_t n, int sms);

@@ -46,7 +46,7 @@ __device__ void sample_sub(const typename T::elem_t* arr, const Workspace<T>& ws
     SubDesc d = ws.subs[j];
     const u32 kk = d.k_target;                 // power of two in [2, 256]
     const u32 alpha = d.alpha;
-    const u32 ns = alpha * kk - 1;             // <= 4095 (host guarantees)
+    const u32 ns = alpha * kk - 1;             // < T::kSampleMax (the planners guarantee)
     const u32 P = pow2_ceil_u32(ns);
     const u64 st = mix64(seed ^ mix64(d.begin * 0x9E3779B97F4A7C15ull + d.level));
     for (u32 i = threadIdx.x; i < P; i += TPB) {
@@ -76,7 +76,7 @@ __device__ void sample_sub(const typename T::elem_t* arr, const Workspace<T>& ws
 template <class T, int TPB>
 __global__ void __launch_bounds__(TPB) k_sample(const typename T::elem_t* arr, Workspace<T> ws, u32 nsub, u64 seed) {
     typedef typename T::key_t K;
-    __shared__ K keys[4096];
+    __shared__ K keys[T::kSampleMax];
     __shared__ K cand[256];
     __shared__ u32 scan_tmp[32];
     if (ws.ls) nsub = ws.ls->nsub;                  // device-planned round
@@ -122,11 +122,13 @@ struct ClassifyRegCfg {
     static constexpr int TILE = 65536 / (int)sizeof(E);        // 64 KiB per tile
     static constexpr int IPT = TILE / TPB;
     static constexpr int B = T::kBlock;
-    static constexpr int CH = 16 / (int)sizeof(E);             // elements per 16-byte chunk (one per lane and block)
-    // grouping area: the new elements of the buckets that emit blocks in a
-    // tile, each bucket's run starting at a parity that makes its blocks
-    // 16-byte aligned (at most one element of padding per bucket and end)
-    static constexpr int GRP = TILE + 2 * kMaxBuckets;
+    // a block is 512 bytes, one 16-byte chunk per lane; 8-byte elements
+    // share a chunk, so a grouping run then starts at the parity that makes
+    // its blocks 16-byte aligned (PAD: at most one element of padding per
+    // bucket and at the end); larger elements are aligned by themselves
+    static constexpr bool PAD = sizeof(E) < 16;
+    // grouping area: the new elements of the buckets that emit blocks in a tile
+    static constexpr int GRP = TILE + (PAD ? 2 * kMaxBuckets : 0);
     static constexpr int MAXBLK = 384;                         // >= (256*(B-1) + TILE) / B
     static constexpr size_t off_buf = 0;
     static constexpr size_t off_grp = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
@@ -146,7 +148,8 @@ struct ClassifyRegCfg {
     static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
     static_assert(kLutCells % TPB == 0 && (size_t)GRP * sizeof(E) >= kLutCells, "table build layout");
     static_assert(TILE <= 65536 && GRP + 64 < 65536, "ranks and grouping offsets are packed in 16 bits");
-    static_assert(B * (int)sizeof(E) == 32 * 16 && CH >= 1, "a block is one 16-byte chunk per lane");
+    static_assert(B * (int)sizeof(E) == 32 * 16 && (sizeof(E) == 8 || sizeof(E) % 16 == 0),
+                  "a block is one 16-byte chunk per lane");
     static_assert(smem_bytes <= 232448, "shared memory of one CTA");
 };
 
@@ -205,6 +208,22 @@ __device__ __forceinline__ void classify_fixed_split(const u64 (&k)[IPT], const 
     }
 }
 
+// The same for keys of several words (the tree kept as whole keys).
+template <class K, int IPT>
+__device__ __forceinline__ void classify_many_k(const K (&k)[IPT], const K* tree, const K* spl, int logL, bool eq,
+                                                int (&bk)[IPT]) {
+    switch (logL) {
+    case 8: classify_fixed<K, IPT, 8>(k, tree, spl, eq, bk); break;
+    case 7: classify_fixed<K, IPT, 7>(k, tree, spl, eq, bk); break;
+    case 6: classify_fixed<K, IPT, 6>(k, tree, spl, eq, bk); break;
+    case 5: classify_fixed<K, IPT, 5>(k, tree, spl, eq, bk); break;
+    case 4: classify_fixed<K, IPT, 4>(k, tree, spl, eq, bk); break;
+    case 3: classify_fixed<K, IPT, 3>(k, tree, spl, eq, bk); break;
+    case 2: classify_fixed<K, IPT, 2>(k, tree, spl, eq, bk); break;
+    default: classify_fixed<K, IPT, 1>(k, tree, spl, eq, bk); break;
+    }
+}
+
 template <int IPT>
 __device__ __forceinline__ void classify_many(const u64 (&k)[IPT], const u32* thi, const u32* tlo, const u64* spl,
                                               int logL, bool eq, int (&bk)[IPT]) {
@@ -219,6 +238,38 @@ __device__ __forceinline__ void classify_many(const u64 (&k)[IPT], const u32* th
     default: classify_fixed_split<IPT, 1>(k, thi, tlo, spl, eq, bk); break;
     }
 }
+
+// Loads subproblem j's search tree and splitters into shared memory for the
+// classification: 64-bit keys as the tree's 32-bit halves (thi, tlo), other
+// keys as whole keys in `tree`.
+template <class T>
+__device__ __forceinline__ void load_class_tree(const Workspace<T>& ws, u32 j, typename T::key_t* tree,
+                                                typename T::key_t* spl, int tid, int nthreads) {
+    typedef typename T::key_t K;
+    for (int i = tid; i < kMaxLeaves; i += nthreads) {
+        const K a = ws.tree[(u64)j * kMaxLeaves + i];
+        if constexpr (std::is_same<K, u64>::value) {
+            ((u32*)tree)[i] = (u32)(a >> 32);
+            ((u32*)tree)[kMaxLeaves + i] = (u32)a;
+        } else {
+            tree[i] = a;
+        }
+        spl[i] = ws.spl[(u64)j * kMaxLeaves + i];
+    }
+}
+
+// Buckets of IPT keys by the tree descent (after load_class_tree).
+template <class K, int IPT>
+__device__ __forceinline__ void classify_keys(const K (&k)[IPT], const K* tree, const K* spl, int logL, bool eq,
+                                              int (&bk)[IPT]) {
+    if constexpr (std::is_same<K, u64>::value) {
+        const u32* thi = (const u32*)tree;
+        classify_many<IPT>(k, thi, thi + kMaxLeaves, spl, logL, eq, bk);
+    } else {
+        classify_many_k<K, IPT>(k, tree, spl, logL, eq, bk);
+    }
+}
+
 
 // Local classification of stripe s (Section 4.1) by the whole CTA
 // (ClassifyCfg<T>::TPB threads, ClassifyCfg<T>::smem_bytes of shared memory).
@@ -246,14 +297,7 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
         const SubDesc sub = ws.subs[sd.sub];
         const int logL = (int)sub.log_leaves;
         const bool eq = sub.eq != 0;
-        u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
-        u32* s_tlo = s_thi + kMaxLeaves;
-        for (int i = tid; i < kMaxLeaves; i += TPB) {
-            const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
-            s_thi[i] = (u32)(a >> 32);
-            s_tlo[i] = (u32)a;
-            s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
-        }
+        load_class_tree<T>(ws, sd.sub, s_tree, s_spl, tid, TPB);
         for (int b = tid; b < kMaxBuckets; b += TPB) { s_fill[b] = 0; s_cnt[b] = 0; s_total[b] = 0; }
         E* A = arr + sd.begin;
         const u32 len = (u32)(sd.end - sd.begin);   // a stripe holds < 2^32 elements
@@ -293,7 +337,7 @@ __device__ void classify_stripe(typename T::elem_t* arr, const Workspace<T>& ws,
                 e[q] = tile[idx < tcount ? idx : 0];
                 k[q] = T::key(e[q]);
             }
-            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+            classify_keys<K, IPT>(k, s_tree, s_spl, logL, eq, bk);
 #pragma unroll
             for (int q = 0; q < IPT; ++q) {
                 if (tid + q * TPB >= tcount) bk[q] = -1;
@@ -431,7 +475,7 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
     typedef ClassifyRegCfg<T> C;
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    constexpr int TPB = C::TPB, NW = C::NW, TILE = C::TILE, IPT = C::IPT, B = C::B, CH = C::CH;
+    constexpr int TPB = C::TPB, NW = C::NW, TILE = C::TILE, IPT = C::IPT, B = C::B;
     constexpr u32 GRP0 = (u32)(C::off_grp / sizeof(E));   // grouping area, in elements from the base
     E* buf = (E*)(smem_raw + C::off_buf);
     E* grp = (E*)(smem_raw + C::off_grp);
@@ -454,14 +498,7 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
     const SubDesc sub = ws.subs[sd.sub];
     const int logL = (int)sub.log_leaves;
     const bool eq = sub.eq != 0;
-    u32* s_thi = (u32*)s_tree;                   // the tree as 32-bit halves
-    u32* s_tlo = s_thi + kMaxLeaves;
-    for (int i = tid; i < kMaxLeaves; i += TPB) {
-        const K a = ws.tree[(u64)sd.sub * kMaxLeaves + i];
-        s_thi[i] = (u32)(a >> 32);
-        s_tlo[i] = (u32)a;
-        s_spl[i] = ws.spl[(u64)sd.sub * kMaxLeaves + i];
-    }
+    load_class_tree<T>(ws, sd.sub, s_tree, s_spl, tid, TPB);
     for (int b = tid; b < kMaxBuckets; b += TPB) {
         s_fill[b] = 0;
         s_cnt[b] = 0;
@@ -474,57 +511,64 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
     const u32 ntiles = (len + TILE - 1) / TILE;
     const bool g16 = ((uintptr_t)A & 15) == 0;   // block stores as 16-byte chunks
     __syncthreads();
-    // The splitter lookup table.  Its cells are linear (aligned to multiples
-    // of 2^shift of the key domain) or logarithmic, whichever puts fewer pairs
-    // of adjacent distinct splitters into one cell (each such pair is a bucket
-    // whose keys all need the binary search); with more than L/16 such pairs
-    // either way, or a tree of fewer than kLutMinLevels levels (a few
-    // comparisons), the stripe keeps the tree descent.  lut_mode: 0 descent,
-    // 1 linear, 2 logarithmic, 3 linear with the cell taken from the key's
-    // high 32 bits (shift >= 32).
+    // The splitter lookup table (keys of one 64-bit word).  Its cells are
+    // linear (aligned to multiples of 2^shift of the key domain) or
+    // logarithmic, whichever puts fewer pairs of adjacent distinct splitters
+    // into one cell (each such pair is a bucket whose keys all need the binary
+    // search); with more than L/16 such pairs either way, or a tree of fewer
+    // than kLutMinLevels levels (a few comparisons), the stripe keeps the tree
+    // descent.  lut_mode: 0 descent, 1 linear, 2 logarithmic, 3 linear with
+    // the cell taken from the key's high 32 bits (shift >= 32).
     const int L = 1 << logL;
-    const u64 lbase = s_spl[1], ltop = s_spl[L - 1];
-    const u32 lsh = lut_abs_shift(lbase, ltop);
-    const u64 lc0 = lbase >> lsh;
+    u64 lbase = 0, lc0 = 0;
+    u32 lsh = 0;
     int lut_mode = 0;
-    {
-        int crowd_lin = 0, crowd_log = 0;
-        if (tid >= 1 && tid + 1 < L) {
-            const u64 a = s_spl[tid], b = s_spl[tid + 1];
-            if (a != b) {
-                crowd_lin = lut_cell_abs(a, lc0, lsh) == lut_cell_abs(b, lc0, lsh) ? 1 : 0;
-                crowd_log = lut_cell_log(a, lbase) == lut_cell_log(b, lbase) ? 1 : 0;
+    if constexpr (std::is_same<K, u64>::value) {
+        const u32* s_thi = (const u32*)s_tree;
+        const u32* s_tlo = s_thi + kMaxLeaves;
+        lbase = s_spl[1];
+        const u64 ltop = s_spl[L - 1];
+        lsh = lut_abs_shift(lbase, ltop);
+        lc0 = lbase >> lsh;
+        {
+            int crowd_lin = 0, crowd_log = 0;
+            if (tid >= 1 && tid + 1 < L) {
+                const u64 a = s_spl[tid], b = s_spl[tid + 1];
+                if (a != b) {
+                    crowd_lin = lut_cell_abs(a, lc0, lsh) == lut_cell_abs(b, lc0, lsh) ? 1 : 0;
+                    crowd_log = lut_cell_log(a, lbase) == lut_cell_log(b, lbase) ? 1 : 0;
+                }
             }
+            const int n_lin = __syncthreads_count(crowd_lin);
+            const int n_log = __syncthreads_count(crowd_log);
+            if (logL >= kLutMinLevels && (n_lin * 16 <= L || n_log * 16 <= L)) lut_mode = n_lin <= n_log ? 1 : 2;
+            if (lut_mode == 1 && lsh >= 32) lut_mode = 3;
         }
-        const int n_lin = __syncthreads_count(crowd_lin);
-        const int n_log = __syncthreads_count(crowd_log);
-        if (logL >= kLutMinLevels && (n_lin * 16 <= L || n_log * 16 <= L)) lut_mode = n_lin <= n_log ? 1 : 2;
-        if (lut_mode == 1 && lsh >= 32) lut_mode = 3;
-    }
-    if (lut_mode != 0) {
-        // i(first key of every cell) by the tree descent into the (still
-        // free) grouping area, then the (lo, hi) entries
-        constexpr int CPT = kLutCells / TPB;
-        unsigned char* s_lo = (unsigned char*)grp;
-        u64 ck[CPT];
-        int ci[CPT];
-        bool ok[CPT];
+        if (lut_mode != 0) {
+            // i(first key of every cell) by the tree descent into the (still
+            // free) grouping area, then the (lo, hi) entries
+            constexpr int CPT = kLutCells / TPB;
+            unsigned char* s_lo = (unsigned char*)grp;
+            u64 ck[CPT];
+            int ci[CPT];
+            bool ok[CPT];
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            const u32 c = (u32)(tid + q * TPB);
-            ok[q] = lut_mode == 2 ? lut_cell_start_log(c, lbase, &ck[q]) : lut_cell_start_abs(c, lc0, lsh, &ck[q]);
-            if (!ok[q]) ck[q] = ltop;
-        }
-        classify_many<CPT>(ck, s_thi, s_tlo, s_spl, logL, false, ci);
+            for (int q = 0; q < CPT; ++q) {
+                const u32 c = (u32)(tid + q * TPB);
+                ok[q] = lut_mode == 2 ? lut_cell_start_log(c, lbase, &ck[q]) : lut_cell_start_abs(c, lc0, lsh, &ck[q]);
+                if (!ok[q]) ck[q] = ltop;
+            }
+            classify_many<CPT>(ck, s_thi, s_tlo, s_spl, logL, false, ci);
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) s_lo[tid + q * TPB] = (unsigned char)(ok[q] ? ci[q] : L - 1);
-        __syncthreads();
-        for (int c = tid; c <= kLutCells; c += TPB) {
-            u32 ent = 0;                          // cell kLutCells (logarithmic map): keys below s_1
-            if (c < kLutCells) ent = (u32)s_lo[c] | ((c + 1 < kLutCells ? (u32)s_lo[c + 1] : (u32)(L - 1)) << 8);
-            s_lut[c] = (unsigned short)ent;
+            for (int q = 0; q < CPT; ++q) s_lo[tid + q * TPB] = (unsigned char)(ok[q] ? ci[q] : L - 1);
+            __syncthreads();
+            for (int c = tid; c <= kLutCells; c += TPB) {
+                u32 ent = 0;                      // cell kLutCells (logarithmic map): keys below s_1
+                if (c < kLutCells) ent = (u32)s_lo[c] | ((c + 1 < kLutCells ? (u32)s_lo[c + 1] : (u32)(L - 1)) << 8);
+                s_lut[c] = (unsigned short)ent;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     E e[IPT], nx[IPT];
@@ -541,41 +585,48 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
     auto classify_rank = [&](u32 tn, u32* cnt) {
         const u32 tcount = len - tn * TILE < (u32)TILE ? len - tn * TILE : (u32)TILE;
         int (&bk)[IPT] = *reinterpret_cast<int(*)[IPT]>(&rk);   // the buckets, then bucket << 16 | rank
-        if (lut_mode == 3) {
-            const u32 c0 = (u32)lc0, shh = lsh - 32;
+        if constexpr (std::is_same<K, u64>::value) {
+            if (lut_mode == 3) {
+                const u32 c0 = (u32)lc0, shh = lsh - 32;
 #pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                const K kq = T::key(e[q]);
-                const int i = lut_refine(kq, s_lut[lut_cell_abs_hi((u32)(kq >> 32), c0, shh)], s_spl);
-                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                for (int q = 0; q < IPT; ++q) {
+                    const K kq = T::key(e[q]);
+                    const int i = lut_refine(kq, s_lut[lut_cell_abs_hi((u32)(kq >> 32), c0, shh)], s_spl);
+                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                }
+            } else if (lut_mode == 1) {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const K kq = T::key(e[q]);
+                    const int i = lut_refine(kq, s_lut[lut_cell_abs(kq, lc0, lsh)], s_spl);
+                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                }
+            } else if (lut_mode == 2) {
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) {
+                    const K kq = T::key(e[q]);
+                    const int i = lut_refine(kq, s_lut[lut_cell_log(kq, lbase)], s_spl);
+                    bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
+                }
+            } else if constexpr (std::is_same<E, K>::value) {
+                // the keys replace the elements for the descent (one fewer
+                // register array), which the inverse map then restores
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) e[q] = T::key(e[q]);
+                classify_keys<K, IPT>(e, s_tree, s_spl, logL, eq, bk);
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) e[q] = T::unkey(e[q]);
+            } else {
+                K k[IPT];
+#pragma unroll
+                for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
+                classify_keys<K, IPT>(k, s_tree, s_spl, logL, eq, bk);
             }
-        } else if (lut_mode == 1) {
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                const K kq = T::key(e[q]);
-                const int i = lut_refine(kq, s_lut[lut_cell_abs(kq, lc0, lsh)], s_spl);
-                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
-            }
-        } else if (lut_mode == 2) {
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) {
-                const K kq = T::key(e[q]);
-                const int i = lut_refine(kq, s_lut[lut_cell_log(kq, lbase)], s_spl);
-                bk[q] = eq ? 2 * i - ((i > 0 && s_spl[i] == kq) ? 1 : 0) : i;
-            }
-        } else if constexpr (std::is_same<E, K>::value) {
-            // the keys replace the elements for the descent (one fewer
-            // register array), which the inverse map then restores
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) e[q] = T::key(e[q]);
-            classify_many<IPT>(e, s_thi, s_tlo, s_spl, logL, eq, bk);
-#pragma unroll
-            for (int q = 0; q < IPT; ++q) e[q] = T::unkey(e[q]);
         } else {
             K k[IPT];
 #pragma unroll
             for (int q = 0; q < IPT; ++q) k[q] = T::key(e[q]);
-            classify_many<IPT>(k, s_thi, s_tlo, s_spl, logL, eq, bk);
+            classify_keys<K, IPT>(k, s_tree, s_spl, logL, eq, bk);
         }
 #pragma unroll
         for (int q = 0; q < IPT; ++q) {
@@ -612,7 +663,8 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
                 const u32 nf = (ff[h] + cc[h]) / B;
-                mine += (nf ? ((cc[h] + (ff[h] & 1u) + 1u) & ~1u) : 0u) | (nf << 16);
+                const u32 run = C::PAD ? ((cc[h] + (ff[h] & 1u) + 1u) & ~1u) : cc[h];
+                mine += (nf ? run : 0u) | (nf << 16);
             }
         }
         u32 x = mine;
@@ -626,12 +678,13 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
         for (int j = 0; j < BPL; ++j) {
             const u32 b = (u32)(b0 + j), cj = cnt[b], fj = s_fill[b], t = fj + cj, nf = t / B, rem = t - nf * B;
             if (nf) {
-                const u32 p = off + (fj & 1u);       // p - f is even: the run's blocks are 16-byte aligned
+                // with PAD, p - f is even: the run's blocks are 16-byte aligned
+                const u32 p = off + (C::PAD ? (fj & 1u) : 0u);
                 s_dst[b] = GRP0 + p;
                 binfo[b] = make_uint2((p - fj + 64u) | (fj << 16) | (rem << 24), nf);
                 for (u32 q = 0; q < nf; ++q) desc[blk + q] = b | (q << 8);
                 blk += nf;
-                off += (cj + (fj & 1u) + 1u) & ~1u;
+                off += C::PAD ? ((cj + (fj & 1u) + 1u) & ~1u) : cj;
             } else {
                 s_dst[b] = b * B + fj;
             }
@@ -663,10 +716,11 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
                 if (lane == 0) set_status(ws.ctr, kStatusInternal);
                 continue;
             }
-            const u32 v0 = (u32)lane * CH;
-            const E* from = v0 < f ? buf + b * B + v0 : grp + (vs + (int)(q * B) + (int)v0);
-            E* to = A + (size_t)slot * B + v0;
-            if constexpr (CH == 2) {
+            if constexpr (sizeof(E) == 8) {
+                // lane's chunk: elements v0, v0 + 1
+                const u32 v0 = (u32)lane * 2;
+                const E* from = v0 < f ? buf + b * B + v0 : grp + (vs + (int)(q * B) + (int)v0);
+                E* to = A + (size_t)slot * B + v0;
                 u64 x0, x1;
                 if (v0 + 1 == f) {                                 // the chunk straddles buffer and run
                     x0 = buf[b * B + v0];
@@ -682,14 +736,26 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
                     to[0] = x0;
                     to[1] = x1;
                 }
+                const u32 rem = bi.x >> 24;
+                if (q == 0 && rem > 0) {
+                    __syncwarp();                                  // block 0 has read the buffer
+                    const E* rs = grp + (vs + (int)(bi.y * B) + (int)v0);
+                    if (v0 < rem) *(uint4*)(buf + b * B + v0) = *(const uint4*)rs;
+                }
             } else {
-                *(uint4*)to = *(const uint4*)from;
-            }
-            const u32 rem = bi.x >> 24;
-            if (q == 0 && rem > 0) {
-                __syncwarp();                                      // block 0 has read the buffer
-                const E* rs = grp + (vs + (int)(bi.y * B) + (int)v0);
-                if (v0 < rem) *(uint4*)(buf + b * B + v0) = *(const uint4*)rs;
+                // lane's chunk: bytes [16 lane, 16 lane + 16) of the block,
+                // inside element v0 (elements of 16 bytes or more)
+                const u32 cb = (u32)lane * 16, v0 = cb / (u32)sizeof(E), co = cb % (u32)sizeof(E);
+                const E* from = v0 < f ? buf + b * B + v0 : grp + (vs + (int)(q * B) + (int)v0);
+                *(uint4*)((char*)(A + (size_t)slot * B) + cb) = *(const uint4*)((const char*)from + co);
+                const u32 rem = bi.x >> 24;
+                if (q == 0 && rem > 0) {
+                    __syncwarp();                                  // block 0 has read the buffer
+                    if (v0 < rem) {
+                        const E* rs = grp + (vs + (int)(bi.y * B) + (int)v0);
+                        *(uint4*)((char*)(buf + b * B + v0) + co) = *(const uint4*)((const char*)rs + co);
+                    }
+                }
             }
         }
     };
@@ -978,7 +1044,9 @@ struct PermuteCfg {
     static constexpr int NW = TPB / 32;
     static constexpr int V = 8;                  // movers per warp (lanes 0..V-1)
     static constexpr int MIN_CTAS = 6;           // register bound; shared memory admits 5 per SM (160 movers)
-    static constexpr int EPL = T::kBlock / 32;   // elements per lane of one block copy
+    // one block (512 bytes) is copied by the warp in chunks of CHB bytes, NCH per lane
+    static constexpr int CHB = sizeof(E) >= 16 ? 16 : (int)sizeof(E);
+    static constexpr int NCH = 512 / CHB / 32;
     static constexpr int MAX_MOVERS_PER_BUCKET = 128;
     // block buffers of the warps, then one copy of the subproblem's tables
     // shared by the CTA (all its warps move blocks of the same subproblem)
@@ -989,7 +1057,7 @@ struct PermuteCfg {
     static constexpr size_t off_gpre = off_delim + (size_t)(kMaxBuckets + 4) * 4;   // u16[1025]
     static constexpr size_t off_misc = off_gpre + 1032 * 2;
     static constexpr size_t smem_bytes = off_misc + 40 * 8;
-    static_assert(T::kBlock % 32 == 0, "block must be a multiple of the warp size");
+    static_assert(T::kBlock * sizeof(E) == 512, "a block is 512 bytes");
 };
 
 // Copy subproblem j's search tree, splitters and delimiters into shared
@@ -1016,7 +1084,7 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
-    constexpr int V = C::V, EPL = C::EPL, B = T::kBlock;
+    constexpr int V = C::V, CHB = C::CHB, NCH = C::NCH, B = T::kBlock;
     const int lane = threadIdx.x & 31;
     const bool is_mover = lane < V;
     const SubDesc sub = ws.subs[j];
@@ -1100,10 +1168,10 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
                 m &= m - 1;
                 const u64 sv = __shfl_sync(0xffffffffu, slot, v);
                 const u32 hb = __shfl_sync(0xffffffffu, hand, v) ^ 1u;      // the free buffer
-                E* dst = wbuf + ((size_t)hb * V + v) * B;
-                const E* src = A + sv * B;
+                char* dst = (char*)(wbuf + ((size_t)hb * V + v) * B);
+                const char* src = (const char*)(A + sv * B);
 #pragma unroll
-                for (int q = 0; q < EPL; ++q) cp_async<sizeof(E)>(dst + lane + 32 * q, src + lane + 32 * q);
+                for (int q = 0; q < NCH; ++q) cp_async<CHB>(dst + CHB * (lane + 32 * q), src + CHB * (lane + 32 * q));
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -1148,10 +1216,14 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
                 m &= m - 1;
                 const u64 sv = __shfl_sync(0xffffffffu, slot, v);
                 const u32 hb = __shfl_sync(0xffffffffu, hand, v);
-                const E* src = wbuf + ((size_t)hb * V + v) * B;
-                E* dst = sv < nbc ? A + sv * B : ovf;
+                const char* src = (const char*)(wbuf + ((size_t)hb * V + v) * B);
+                char* dst = (char*)(sv < nbc ? A + sv * B : ovf);
 #pragma unroll
-                for (int q = 0; q < EPL; ++q) dst[lane + 32 * q] = src[lane + 32 * q];
+                for (int q = 0; q < NCH; ++q) {
+                    const int off = CHB * (lane + 32 * q);
+                    if constexpr (CHB == 16) *(uint4*)(dst + off) = *(const uint4*)(src + off);
+                    else *(u64*)(dst + off) = *(const u64*)(src + off);
+                }
             }
             __syncwarp();
         }
@@ -1192,7 +1264,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
-    constexpr int TPB = C::TPB, NW = C::NW, V = C::V, EPL = C::EPL, B = T::kBlock;
+    constexpr int TPB = C::TPB, NW = C::NW, V = C::V, B = T::kBlock;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned short* s_gpre = (unsigned short*)(smem_raw + C::off_gpre);
     u64* s_misc = (u64*)(smem_raw + C::off_misc);   // [0] total, [1..33] scan tmp

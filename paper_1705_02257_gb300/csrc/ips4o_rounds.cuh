@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
         if (K == 0) K = seg_leaves(n_i, (u64)pa.base_cap, pa.k_max);
         u32 alpha = pa.alpha > 0 ? pa.alpha : 16u;
         if (c_class_alpha[cls]) alpha = c_class_alpha[cls];
-        if (alpha * K > 4096) alpha = 4096 / K;
+        if (alpha * K > (u32)T::kSampleMax) alpha = (u32)T::kSampleMax / K;
         if (alpha < 1) alpha = 1;
         k_i = K;
         SubDesc sd;

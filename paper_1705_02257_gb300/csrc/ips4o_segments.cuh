@@ -46,7 +46,7 @@ struct SegCfg {
     typedef BaseLarge<T> Base;
     static_assert(Base::TPB == TPB, "the base case runs on the whole CTA");
     // phases reuse one shared-memory area
-    static constexpr size_t sample_bytes = 4096 * sizeof(K) + 256 * sizeof(K) + 32 * 4;
+    static constexpr size_t sample_bytes = (size_t)T::kSampleMax * sizeof(K) + 256 * sizeof(K) + 32 * 4;
     static constexpr size_t prefix_bytes = 32 * 8 + 2 * kMaxStripesPerSub * 4 + (kMaxBuckets + 1) * 4;
     static constexpr size_t perm_buf = (size_t)NWP * 2 * PermuteCfg<T>::V * B * sizeof(E);
     static constexpr size_t perm_bytes = perm_buf + 2 * kMaxLeaves * sizeof(K) + (kMaxBuckets + 1) * 4;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(SegCfg<T>::TPB, 1)
             u32 K_ = c_class_leaves[cls];
             if (K_ == 0) K_ = seg_leaves(t.n, (u64)T::kBaseSmall, k_max);
             u32 alpha = c_class_alpha[cls] ? c_class_alpha[cls] : 16u;
-            if (alpha * K_ > 4096) alpha = 4096 / K_;
+            if (alpha * K_ > (u32)T::kSampleMax) alpha = (u32)T::kSampleMax / K_;
             SubDesc sd;
             sd.begin = t.begin;
             sd.n = t.n;
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(SegCfg<T>::TPB, 1)
         __syncthreads();
         {
             K* keys = (K*)smem_raw;
-            K* cand = keys + 4096;
+            K* cand = keys + T::kSampleMax;
             u32* scan = (u32*)(cand + 256);
             sample_sub<T, TPB>(arr, ws, j, seed, keys, cand, scan);
         }

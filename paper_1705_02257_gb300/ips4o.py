@@ -20,9 +20,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 # with different tuning constants); by default the in-tree build is loaded.
 LIB_PATH = os.environ.get("IPS4O_LIBRARY") or os.path.join(_HERE, "libips4o_gb300.so")
 
-U64, F64, PAIR_U64, REC100_K10 = 0, 1, 2, 3
-KEY_TYPES = {"u64": U64, "f64": F64, "pair": PAIR_U64, "rec100": REC100_K10}
-ELEM_SIZE = {U64: 8, F64: 8, PAIR_U64: 16, REC100_K10: 100}
+U64, F64, PAIR_U64, REC100_K10, QUARTET_U64 = 0, 1, 2, 3, 4
+KEY_TYPES = {"u64": U64, "f64": F64, "pair": PAIR_U64, "rec100": REC100_K10, "quartet": QUARTET_U64}
+ELEM_SIZE = {U64: 8, F64: 8, PAIR_U64: 16, REC100_K10: 100, QUARTET_U64: 32}
 
 STATUS = {
     0: "IPS4O_OK", 1: "IPS4O_ERR_INVALID_ARG", 2: "IPS4O_ERR_UNSUPPORTED_TYPE",

@@ -112,3 +112,16 @@ def test_sorted_input_skips_blocks_already_in_place(ips4o):
     assert moved <= 0.35 * slots, counts
     moved_u, skipped_u, slots_u = counts["uniform"]
     assert moved_u >= 0.9 * slots_u and skipped_u <= 0.01 * slots_u, counts
+
+
+def test_quartet_2pow25(ips4o):
+    # 2^25 quartets (1 GiB): sorted by (k0, k1, k2), the input's multiset
+    n = 1 << 25
+    a = inputs.quartet(n, "uniform")
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1)).cuda()
+    ips4o.sort(t, "quartet")
+    torch.cuda.synchronize()
+    out = t.cpu().numpy().view(inputs.QUARTET_DTYPE)
+    del t
+    assert oracle.is_sorted(out, "quartet")
+    assert oracle.multiset_hash(out, "quartet") == oracle.multiset_hash(a, "quartet")

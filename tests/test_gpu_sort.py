@@ -391,3 +391,42 @@ def test_capture_without_reserved_workspace_is_refused(ips4o):
     g.replay()
     torch.cuda.synchronize()
     assert int(x.sum().item()) == 16
+
+
+def _check_quartet(got, a):
+    """Quartets: the (k0, k1, k2) sequence equals the oracle's bit for bit;
+    the elements are the input's multiset (payload order among equal keys is
+    free, the method not being stable)."""
+    exp = oracle.sort(a, "quartet")
+    for f in ("k0", "k1", "k2"):
+        assert np.array_equal(got[f], exp[f]), f
+    assert oracle.multiset_hash(got, "quartet") == oracle.multiset_hash(a, "quartet")
+
+
+@pytest.mark.parametrize("dist", inputs.DISTRIBUTIONS)
+@pytest.mark.parametrize("n", [1 << 20, 1_500_007])
+def test_quartet(ips4o, dist, n):
+    """Section 5's Quartet: three key words compared lexicographically (the
+    generator repeats first words and draws the second from four values, so
+    later words decide many comparisons), one payload word, sorted in place."""
+    a = inputs.quartet(n, dist)
+    _check_quartet(gpu_sort(ips4o, a, "quartet"), a)
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 15, 16, 17, 1023, 1024, 1025, 4096, 4097, 100_003])
+def test_quartet_edge_sizes(ips4o, n):
+    a = inputs.quartet(n, "two_dup")
+    _check_quartet(gpu_sort(ips4o, a, "quartet"), a)
+
+
+def test_quartet_segmented(ips4o):
+    lengths = inputs.log_uniform_lengths(300, 4, 17)
+    off = np.concatenate([[0], np.cumsum(lengths)]).astype(np.uint64)
+    a = inputs.quartet(int(off[-1]), "root_dup")
+    t = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1).copy()).cuda()
+    ips4o.sort_segmented(t, off, "quartet")
+    torch.cuda.synchronize()
+    got = t.cpu().numpy().view(inputs.QUARTET_DTYPE)
+    for i in range(0, len(lengths), 7):
+        lo, hi = int(off[i]), int(off[i + 1])
+        _check_quartet(got[lo:hi], a[lo:hi])
