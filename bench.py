@@ -261,6 +261,9 @@ def run_gpu(args):
     base_params = {}
     if args.stripes_per_sm > 0:
         base_params["stripes_per_sm"] = args.stripes_per_sm
+    if args.record_path:
+        base_params["record_path"] = args.record_path
+    if base_params:
         ips4o.set_params(**base_params)
 
     def one_step():
@@ -315,7 +318,8 @@ def run_gpu(args):
     # algorithmic bytes per launch (Appendix B I/O volume): classification and
     # block permutation each read and write the elements of the launch once.
     # Records are distributed as 16-byte (key prefix, index) pairs.
-    dist_elem = 16 if kt == "rec100" else elem
+    rec_blocks = kt == "rec100" and args.record_path == 1        # records moved in place, not through pairs
+    dist_elem = 16 if kt == "rec100" and not rec_blocks else elem
     # elements classified over all levels of one sort (a deeper level often
     # holds only a few buckets): the classification and permutation volume
     distributed = stats["elements_distributed"] or n * levels
@@ -335,13 +339,13 @@ def run_gpu(args):
     value = n * world * args.steps / (total_ms * 1e-3)
     # the sort's roofline uses the nominal number of levels, log_k(n / base
     # case) with k = 256, the same bar for every distribution
-    base_cap = ips4o.ips4o_base_case_capacity(ips4o.KEY_TYPES["pair" if kt == "rec100" else kt])
+    base_cap = 1024 if rec_blocks else ips4o.ips4o_base_case_capacity(ips4o.KEY_TYPES["pair" if kt == "rec100" else kt])
     nominal_levels, m = 0, n
     while m > base_cap:
         m = (m + 255) // 256
         nominal_levels += 1
     alg_sort = (4 * nominal_levels + 2) * n * dist_elem
-    if kt == "rec100":
+    if kt == "rec100" and not rec_blocks:
         # key extraction (12 bytes read, 16 written), input copy (read + write)
         # and the gather (pair read, record read + write)
         alg_sort += n * (12 + 16) + 2 * n * elem + n * (16 + 2 * elem)
@@ -393,8 +397,9 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_NAME[kt], "data": "synthetic",
-        "config": {"workload": f"{'sort' if kt == 'rec100' else 'in-place sort'} of 2^{args.log2n} {KT_LABEL[kt]}, "
-                               f"{args.dist} (seed 1)",
+        "config": {"workload": f"{'sort' if kt == 'rec100' and not rec_blocks else 'in-place sort'} of 2^{args.log2n} "
+                               f"{KT_LABEL[kt]}, {args.dist} (seed 1)"
+                               f"{' (in-place block path)' if rec_blocks else (' (key + index indirection)' if kt == 'rec100' else '')}",
                    "n": n, "key_type": kt, "distribution": args.dist,
                    "l2": f"input {n * elem / 2**30:.2f} GiB per step, larger than the 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}", "levels": levels},
@@ -746,6 +751,8 @@ def main():
     ap.add_argument("--verify-segments", type=int, default=200, help="batched: arrays checked against the oracle")
     ap.add_argument("--autotune", action="store_true",
                     help="batched: tune leaves / alpha per size class first and sort with that table")
+    ap.add_argument("--record-path", type=int, default=0, choices=[0, 1],
+                    help="100-byte records: 0 key + index indirection (default), 1 in-place blocks")
     ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2],
                     help="batched: 0 automatic, 1 level by level, 2 one CTA per array")
     args = ap.parse_args()

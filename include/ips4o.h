@@ -100,6 +100,11 @@ typedef struct {
                                ips4o_sort_segmented_async) */
     uint32_t spin_limit;    /* polls of every bounded device wait before it gives up and the call
                                returns IPS4O_ERR_TIMEOUT; 0 selects the default (2^22, about 0.3 s) */
+    int record_path;        /* 100-byte records: 0 key + index indirection (default; records with
+                               equal keys keep their input order; 132 bytes of extra device memory
+                               per record), 1 the records moved in place through the distribution
+                               steps in blocks of 5 (not stable; workspace independent of the
+                               record size but for the blocks) */
 } ips4o_params;
 
 /* Parameters of the distribution steps per size class, as an autotuner picks

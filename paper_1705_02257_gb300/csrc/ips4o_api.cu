@@ -511,6 +511,7 @@ ips4o_status ips4o_set_params(const ips4o_params* p) {
     if (p->stripes_per_sm < 1 || p->stripes_per_sm > 16) return IPS4O_ERR_INVALID_ARG;
     if (p->alpha > 4095) return IPS4O_ERR_INVALID_ARG;
     if (p->segment_scheduler < 0 || p->segment_scheduler > 2) return IPS4O_ERR_INVALID_ARG;
+    if (p->record_path < 0 || p->record_path > 1) return IPS4O_ERR_INVALID_ARG;
     g_params = *p;
     return IPS4O_OK;
 }

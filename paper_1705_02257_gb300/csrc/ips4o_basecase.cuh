@@ -31,6 +31,10 @@ template <>
 __device__ __forceinline__ u64 key_min<u64>() { return 0ull; }
 template <>
 __device__ __forceinline__ QKey key_min<QKey>() { return QKey{0ull, 0ull, 0ull}; }
+template <>
+__device__ __forceinline__ RKey key_max<RKey>() { return RKey{~0ull, ~0ull}; }
+template <>
+__device__ __forceinline__ RKey key_min<RKey>() { return RKey{0ull, 0ull}; }
 
 __device__ __forceinline__ u32 pow2_ceil_u32(u32 x) {
     return x <= 1 ? 1u : (1u << (32 - __clz(x - 1)));
@@ -123,7 +127,6 @@ struct BaseCfg {
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
     static_assert(CAP <= 65535, "ranks are packed in 16 bits");
-    static_assert(EPT % 2 == 0, "ranks are packed two per register");
     static_assert(MAXSUB % TPB == 0, "whole sub-bucket counters per thread");
     __device__ static __forceinline__ u32 pad(u32 s) { return s + (s >> 5); }
 };
@@ -247,9 +250,9 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         const u64 d = (T::sub_key(k) - lo_w) >> shift;
         return d < (u64)KB ? (u32)d : KB - 1;
     };
-    u32 rk2[EPT / 2];
+    u32 rk2[(EPT + 1) / 2];                          // arrival ranks, two 16-bit ranks per register
 #pragma unroll
-    for (int q = 0; q < EPT / 2; ++q) rk2[q] = 0;
+    for (int q = 0; q < (EPT + 1) / 2; ++q) rk2[q] = 0;
 #pragma unroll
     for (int q = 0; q < EPT; ++q) {
         const u32 idx = tid + q * TPB;

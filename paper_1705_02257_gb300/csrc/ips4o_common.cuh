@@ -134,11 +134,57 @@ struct TQuartet {
     __host__ __device__ static inline u64 sub_key(const key_t& k) { return k.a; }
 };
 
+// 100-byte record (Section 5's 100Bytes), moved in place by the block path:
+// key = bytes [0, 10) compared as unsigned bytes, i.e. (big-endian bytes
+// 0..7, big-endian bytes 8..9); 4-byte aligned.
+struct RKey {
+    u64 hi, lo;
+};
+__host__ __device__ __forceinline__ bool operator<(const RKey& x, const RKey& y) {
+    return x.hi < y.hi || (x.hi == y.hi && x.lo < y.lo);
+}
+__host__ __device__ __forceinline__ bool operator==(const RKey& x, const RKey& y) { return x.hi == y.hi && x.lo == y.lo; }
+__host__ __device__ __forceinline__ bool operator!=(const RKey& x, const RKey& y) { return !(x == y); }
+__host__ __device__ __forceinline__ bool operator>(const RKey& x, const RKey& y) { return y < x; }
+__host__ __device__ __forceinline__ bool operator<=(const RKey& x, const RKey& y) { return !(y < x); }
+__host__ __device__ __forceinline__ bool operator>=(const RKey& x, const RKey& y) { return !(x < y); }
+
+struct alignas(4) RecElem {
+    u32 w[25];
+};
+
+__host__ __device__ __forceinline__ u32 bswap32(u32 x) {
+#ifdef __CUDA_ARCH__
+    return __byte_perm(x, 0, 0x0123);
+#else
+    return (x >> 24) | ((x >> 8) & 0xff00u) | ((x << 8) & 0xff0000u) | (x << 24);
+#endif
+}
+
+struct TRec {
+    typedef RecElem elem_t;
+    typedef RKey key_t;
+    static constexpr int kId = 4;
+    static constexpr int kBlock = 5;                  // 5 x 100 B = 500 B
+    static constexpr int kBaseTiny = 256;
+    static constexpr int kBaseSmall = 512;
+    static constexpr int kBaseCap = 1024;              // 100 KB of shared memory
+    static constexpr int kSampleMax = 2048;            // 32 KiB of keys
+    __host__ __device__ static inline key_t key(const elem_t& e) {
+        return RKey{((u64)bswap32(e.w[0]) << 32) | bswap32(e.w[1]), (u64)(((e.w[2] & 0xffu) << 8) | ((e.w[2] >> 8) & 0xffu))};
+    }
+    __host__ __device__ static inline u64 key_bits(const key_t& k) { return k.hi; }
+    __host__ __device__ static inline u64 sub_key(const key_t& k) { return k.hi; }
+};
+
 // Warp shuffle of a key of any of the types above.
 __device__ __forceinline__ u64 shfl_xor_key(u64 v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ QKey shfl_xor_key(const QKey& v, int o) {
     return QKey{__shfl_xor_sync(0xffffffffu, v.a, o), __shfl_xor_sync(0xffffffffu, v.b, o),
                 __shfl_xor_sync(0xffffffffu, v.c, o)};
+}
+__device__ __forceinline__ RKey shfl_xor_key(const RKey& v, int o) {
+    return RKey{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
 }
 
 // ------------------------------------------------------------ descriptors
@@ -276,6 +322,10 @@ template <>
 __device__ __forceinline__ void cp_async<16>(void* smem, const void* gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(smem)), "l"(gmem)
                  : "memory");
+}
+template <>
+__device__ __forceinline__ void cp_async<4>(void* smem, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
 }
 template <>
 __device__ __forceinline__ void cp_async<32>(void* smem, const void* gmem) {

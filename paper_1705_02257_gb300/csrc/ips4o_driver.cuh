@@ -216,9 +216,10 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
 // leaves the planner gives that size (the class table, else leaves_for),
 // down to the recursion threshold.  When the last level's nominal buckets
 // come within a factor of 4 of the threshold, sampling may leave some above
-// it, and one more round is added; one more round again takes a level with
-// more subproblems than nominal (skewed keys).  Rarer stragglers, and any
-// deeper recursion, go to the segment scheduler after the last round.
+// it, and one more round is added; two more rounds take a level with more
+// subproblems than nominal and one level more than nominal (skewed keys,
+// such as Exponential's).  Rarer stragglers, and any deeper recursion, go to
+// the segment scheduler after the last round.
 inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
     double subs = 1.0, m = (double)n;
     u32 r = 0;
@@ -229,7 +230,7 @@ inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
         subs *= K;
         m /= K;
     }
-    return r + 1 + (m * 4.0 > (double)cap ? 1u : 0u);
+    return r + 2 + (m * 4.0 > (double)cap ? 1u : 0u);
 }
 
 #define IPS4O_CUDA(call)                                    \
@@ -257,8 +258,9 @@ ips4o_status set_kernel_attributes(DeviceState& st) {
                                     (int)BaseLarge<T>::smem_bytes));
     IPS4O_CUDA(cudaFuncSetAttribute(k_permute<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)PermuteCfg<T>::smem_bytes));
-    IPS4O_CUDA(cudaFuncSetAttribute(k_segments<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)SegCfg<T>::smem_bytes));
+    if constexpr (!std::is_same<T, TRec>::value)   // 100-byte records: host-planned levels only
+        IPS4O_CUDA(cudaFuncSetAttribute(k_segments<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)SegCfg<T>::smem_bytes));
     int occ = 0;
     IPS4O_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_permute<T>, PermuteCfg<T>::TPB,
                                                              PermuteCfg<T>::smem_bytes));

@@ -23,8 +23,8 @@ struct DeviceState {
     void* d_aux = nullptr;          // 100-byte records: pairs, input copy, run bounds
     size_t aux_bytes = 0;
     unsigned* d_status = nullptr;   // status word of the last enqueue-only call on this stream
-    bool attrs_ready[4] = {false, false, false, false};   // kernel attributes set, per element type
-    int permute_grid[4] = {0, 0, 0, 0};
+    bool attrs_ready[5] = {false, false, false, false, false};   // kernel attributes set, per element type
+    int permute_grid[5] = {0, 0, 0, 0, 0};
     std::vector<cudaEvent_t> events;
     struct Timed { int phase; int ev; };
     std::vector<Timed> timed;       // profiled launches whose events have not been read yet
@@ -49,7 +49,7 @@ ips4o_status finalize_pending(DeviceState& st);
 ips4o_status collect_profile_events(DeviceState& st);
 
 // The library's default parameters (what ips4o_set_params(NULL) restores).
-constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0};
+constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0, 0};
 
 DeviceState* stream_state(void* stream, cudaError_t* err);   // state of (current device, stream)
 DeviceState* current_device_state(cudaError_t* err);          // state of (current device, NULL stream)

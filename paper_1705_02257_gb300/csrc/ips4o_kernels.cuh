@@ -119,10 +119,11 @@ struct ClassifyRegCfg {
     typedef typename T::key_t K;
     static constexpr int TPB = 512;
     static constexpr int NW = TPB / 32;
-    static constexpr int TILE = 65536 / (int)sizeof(E);        // 64 KiB per tile
+    static constexpr int TILE = 65536 / (int)sizeof(E) / TPB * TPB;   // about 64 KiB per tile
     static constexpr int IPT = TILE / TPB;
     static constexpr int B = T::kBlock;
-    // a block is 512 bytes, one 16-byte chunk per lane; 8-byte elements
+    // a block is 512 bytes, one 16-byte chunk per lane (100-byte records:
+    // 500 bytes in 4-byte words); 8-byte elements
     // share a chunk, so a grouping run then starts at the parity that makes
     // its blocks 16-byte aligned (PAD: at most one element of padding per
     // bucket and at the end); larger elements are aligned by themselves
@@ -148,8 +149,10 @@ struct ClassifyRegCfg {
     static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
     static_assert(kLutCells % TPB == 0 && (size_t)GRP * sizeof(E) >= kLutCells, "table build layout");
     static_assert(TILE <= 65536 && GRP + 64 < 65536, "ranks and grouping offsets are packed in 16 bits");
-    static_assert(B * (int)sizeof(E) == 32 * 16 && (sizeof(E) == 8 || sizeof(E) % 16 == 0),
-                  "a block is one 16-byte chunk per lane");
+    static_assert((B * (int)sizeof(E) == 32 * 16 && (sizeof(E) == 8 || sizeof(E) % 16 == 0)) ||
+                      (sizeof(E) % 4 == 0 && B * (int)sizeof(E) <= 512),
+                  "a block is one 16-byte chunk per lane, or at most 512 bytes of 4-byte words");
+    static_assert(IPT >= 1, "at least one element per thread and tile");
     static_assert(smem_bytes <= 232448, "shared memory of one CTA");
 };
 
@@ -742,6 +745,23 @@ __device__ void classify_stripe_reg(typename T::elem_t* arr, const typename T::e
                     const E* rs = grp + (vs + (int)(bi.y * B) + (int)v0);
                     if (v0 < rem) *(uint4*)(buf + b * B + v0) = *(const uint4*)rs;
                 }
+            } else if constexpr (sizeof(E) % 16 != 0) {
+                // 4-byte words (100-byte records): word wi of the block lies
+                // in element wi / WPE
+                constexpr u32 WPE = (u32)sizeof(E) / 4, WPB = (u32)B * WPE;
+                u32* to = (u32*)(A + (size_t)slot * B);
+                for (u32 wi = (u32)lane; wi < WPB; wi += 32) {
+                    const u32 v = wi / WPE;
+                    const E* from = v < f ? buf + b * B + v : grp + (vs + (int)(q * B) + (int)v);
+                    to[wi] = ((const u32*)from)[wi - v * WPE];
+                }
+                const u32 rem = bi.x >> 24;
+                if (q == 0 && rem > 0) {
+                    __syncwarp();                                  // block 0 has read the buffer
+                    const E* rs = grp + (vs + (int)(bi.y * B));
+                    for (u32 wi = (u32)lane; wi < rem * WPE; wi += 32)
+                        ((u32*)(buf + b * B))[wi] = ((const u32*)rs)[wi];
+                }
             } else {
                 // lane's chunk: bytes [16 lane, 16 lane + 16) of the block,
                 // inside element v0 (elements of 16 bytes or more)
@@ -1044,9 +1064,12 @@ struct PermuteCfg {
     static constexpr int NW = TPB / 32;
     static constexpr int V = 8;                  // movers per warp (lanes 0..V-1)
     static constexpr int MIN_CTAS = 6;           // register bound; shared memory admits 5 per SM (160 movers)
-    // one block (512 bytes) is copied by the warp in chunks of CHB bytes, NCH per lane
-    static constexpr int CHB = sizeof(E) >= 16 ? 16 : (int)sizeof(E);
-    static constexpr int NCH = 512 / CHB / 32;
+    // one block (512 bytes; 500 for 100-byte records) is copied by the warp
+    // in chunks of CHB bytes, at most NCH per lane
+    static constexpr int BB = T::kBlock * (int)sizeof(E);
+    static constexpr int CHB = sizeof(E) % 16 == 0 ? 16 : (sizeof(E) % 8 == 0 ? 8 : 4);
+    static constexpr int NCHT = BB / CHB;
+    static constexpr int NCH = (NCHT + 31) / 32;
     static constexpr int MAX_MOVERS_PER_BUCKET = 128;
     // block buffers of the warps, then one copy of the subproblem's tables
     // shared by the CTA (all its warps move blocks of the same subproblem)
@@ -1057,7 +1080,7 @@ struct PermuteCfg {
     static constexpr size_t off_gpre = off_delim + (size_t)(kMaxBuckets + 4) * 4;   // u16[1025]
     static constexpr size_t off_misc = off_gpre + 1032 * 2;
     static constexpr size_t smem_bytes = off_misc + 40 * 8;
-    static_assert(T::kBlock * sizeof(E) == 512, "a block is 512 bytes");
+    static_assert(BB <= 512 && BB % CHB == 0, "a block is at most 512 bytes of whole chunks");
 };
 
 // Copy subproblem j's search tree, splitters and delimiters into shared
@@ -1084,7 +1107,7 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
-    constexpr int V = C::V, CHB = C::CHB, NCH = C::NCH, B = T::kBlock;
+    constexpr int V = C::V, CHB = C::CHB, NCH = C::NCH, NCHT = C::NCHT, B = T::kBlock;
     const int lane = threadIdx.x & 31;
     const bool is_mover = lane < V;
     const SubDesc sub = ws.subs[j];
@@ -1171,7 +1194,9 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
                 char* dst = (char*)(wbuf + ((size_t)hb * V + v) * B);
                 const char* src = (const char*)(A + sv * B);
 #pragma unroll
-                for (int q = 0; q < NCH; ++q) cp_async<CHB>(dst + CHB * (lane + 32 * q), src + CHB * (lane + 32 * q));
+                for (int q = 0; q < NCH; ++q)
+                    if (NCHT % 32 == 0 || lane + 32 * q < NCHT)
+                        cp_async<CHB>(dst + CHB * (lane + 32 * q), src + CHB * (lane + 32 * q));
             }
             cp_async_commit();
             cp_async_wait<0>();
@@ -1220,9 +1245,11 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
                 char* dst = (char*)(sv < nbc ? A + sv * B : ovf);
 #pragma unroll
                 for (int q = 0; q < NCH; ++q) {
+                    if (NCHT % 32 != 0 && lane + 32 * q >= NCHT) continue;
                     const int off = CHB * (lane + 32 * q);
                     if constexpr (CHB == 16) *(uint4*)(dst + off) = *(const uint4*)(src + off);
-                    else *(u64*)(dst + off) = *(const u64*)(src + off);
+                    else if constexpr (CHB == 8) *(u64*)(dst + off) = *(const u64*)(src + off);
+                    else *(u32*)(dst + off) = *(const u32*)(src + off);
                 }
             }
             __syncwarp();

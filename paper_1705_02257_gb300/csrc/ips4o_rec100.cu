@@ -1,23 +1,29 @@
 // ips4o_rec100.cu — 100-byte records (Section 5 "100Bytes": a 10-byte key
-// compared as unsigned bytes, then 90 bytes of payload) by key + index
-// indirection.
+// compared as unsigned bytes, then 90 bytes of payload), two ways.
 //
-// Moving 100-byte elements through the distribution levels costs 100 bytes
-// per element per pass, and the element does not fit the 512-byte block and
-// shared-memory buffer design of the other types.  The paper notes that for
-// such large elements its in-place method moves every element twice per
-// level (Section 6, comparison with s^3-sort).  Here the records are instead
-// represented by 16-byte pairs
+// Key + index indirection (the default).  Moving 100-byte elements through
+// the distribution levels costs 100 bytes per element per pass; the paper
+// notes that for such large elements its in-place method moves every element
+// twice per level (Section 6, comparison with s^3-sort).  Here the records
+// are instead represented by 16-byte pairs
 //     key     = bytes 0..7 of the record as a big-endian integer,
 //     payload = bytes 8..9 as a big-endian 16-bit integer << 48 | record index,
 // which are sorted by the pair path; runs of equal 8-byte prefixes are then
 // sorted again by payload (bytes 8..9, then index), and finally every record
 // is gathered once from a copy of the input to its place.  The result is the
 // records in key order, records with equal keys in their input order.
-//
 // Extra device memory: 16 bytes (pairs) + 100 bytes (input copy) + 16 bytes
-// (run bounds) per record, besides the pair sort's own workspace; this entry
-// point is not in place.
+// (run bounds) per record, besides the pair sort's own workspace; not in
+// place.
+//
+// In-place blocks (params.record_path = 1).  The records themselves go
+// through the distribution steps of the other types, in blocks of 5 records
+// (500 bytes, copied in 4-byte words) with keys (bytes 0..7, bytes 8..9)
+// compared by the tree descent, down to a shared-memory base case of up to
+// 1024 records; the levels are planned on the host.  In place (workspace
+// O(k b t + #subproblems)); not stable.
+#include "ips4o_driver.cuh"
+
 #include <algorithm>
 #include <vector>
 
@@ -28,8 +34,6 @@ namespace ips4o {
 
 constexpr int kRecBytes = 100;
 constexpr int kRecWords = kRecBytes / 4;
-
-__device__ __forceinline__ u32 bswap32(u32 x) { return __byte_perm(x, 0, 0x0123); }
 
 // pairs[i] = {big-endian bytes 0..7, big-endian bytes 8..9 << 48 | i}
 __global__ void k_rec_extract(const u32* __restrict__ rec, u64 n, PairElem* __restrict__ pairs) {
@@ -83,7 +87,14 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 // pairs [16 n] | input copy [100 n] | run begins, run ends [n / 2 + 1 each] | counts
 size_t rec100_aux_bytes(size_t n) { return align256(n * (16 + kRecBytes)) + 2 * (n / 2 + 1) * 8 + 256; }
 
+// The block path: the records sorted in place by the distribution steps.
+static ips4o_status sort_rec100_blocks(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    Driver<TRec> drv(st, s);
+    return drv.run((RecElem*)d, (u64)n, nullptr);
+}
+
 ips4o_status sort_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    if (global_params().record_path == 1) return sort_rec100_blocks(st, d, n, s);
     ips4o_status rc = ensure_device_buffer(&st.d_aux, &st.aux_bytes, rec100_aux_bytes(n));
     if (rc != IPS4O_OK) return rc;
     char* aux = (char*)st.d_aux;

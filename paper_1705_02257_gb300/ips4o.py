@@ -47,7 +47,7 @@ class Ips4oError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("alpha", ctypes.c_int), ("base_case_max", ctypes.c_int),
                 ("stripes_per_sm", ctypes.c_int), ("profile", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("segment_scheduler", ctypes.c_int), ("spin_limit", ctypes.c_uint32)]
+                ("segment_scheduler", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("record_path", ctypes.c_int)]
 
 
 class ClassParams(ctypes.Structure):

@@ -430,3 +430,26 @@ def test_quartet_segmented(ips4o):
     for i in range(0, len(lengths), 7):
         lo, hi = int(off[i]), int(off[i + 1])
         _check_quartet(got[lo:hi], a[lo:hi])
+
+
+@pytest.mark.parametrize("dist", ["uniform", "ones", "two_dup", "root_dup", "sorted", "exponential"])
+@pytest.mark.parametrize("n", [1, 2, 5, 1023, 1025, 100_003, 1 << 20])
+def test_rec100_block_path(ips4o, dist, n):
+    """100-byte records moved in place through the distribution steps
+    (params.record_path = 1): the key sequence equals the oracle's bit for
+    bit and the records are the input's multiset (the block path is not
+    stable, unlike the indirection)."""
+    a = inputs.rec100(n, dist)
+    ips4o.set_params(record_path=1)
+    try:
+        t = torch.from_numpy(a.reshape(-1).copy()).cuda()
+        ips4o.sort(t, "rec100")
+        torch.cuda.synchronize()
+    finally:
+        ips4o.reset_params()
+    got = t.cpu().numpy().reshape(n, 100)
+    exp = oracle.sort(a, "rec100")
+    gh, gl = _rec_keys(got)
+    eh, el = _rec_keys(exp)
+    assert np.array_equal(gh, eh) and np.array_equal(gl, el)
+    assert oracle.multiset_hash(got, "rec100") == oracle.multiset_hash(a, "rec100")
