@@ -120,10 +120,10 @@ struct BaseCfg {
     // different banks for the 32 lanes of a warp
     static constexpr u32 PADDED = MAXSUB + MAXSUB / 32 + 1;
     static constexpr size_t off_data = 0;
-    static constexpr size_t off_off = off_data + (size_t)CAP * sizeof(E);   // u32[PADDED]
-    static constexpr size_t off_tmp = off_off + ((size_t)PADDED * 4 + 15) / 16 * 16;
-    static constexpr size_t off_big = off_tmp + 64 * sizeof(K);             // u32[MAXBIG + 1]
-    static constexpr size_t smem_bytes = off_big + (MAXBIG + 1) * 4;
+    static constexpr size_t off_off = a16(off_data + (size_t)CAP * sizeof(E));   // u32[PADDED]
+    static constexpr size_t off_tmp = a16(off_off + ((size_t)PADDED * 4 + 15) / 16 * 16);
+    static constexpr size_t off_big = a16(off_tmp + 64 * sizeof(K));             // u32[MAXBIG + 1]
+    static constexpr size_t smem_bytes = a16(off_big + (MAXBIG + 1) * 4);
     static constexpr int SUBS_PER_THREAD = MAXSUB / TPB;
     static_assert(CAP % TPB == 0, "capacity must be a multiple of the CTA size");
     static_assert(CAP <= 65535, "ranks are packed in 16 bits");
@@ -294,7 +294,9 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     __syncthreads();
     // final position = sub-bucket start + rank of the key within it
     // (elements of large sub-buckets are placed below)
-#pragma unroll
+    // (not unrolled: the loop body holds the rank loop, and the unrolled copies
+    // cost more in instruction fetch than they save)
+#pragma unroll 1
     for (int q = 0; q < EPT; ++q) {
         const u32 i = tid + q * TPB;
         if (i < m) {

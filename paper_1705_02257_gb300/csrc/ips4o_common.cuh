@@ -392,6 +392,10 @@ __device__ __forceinline__ u64 mix64(u64 z) {
 
 __host__ __device__ __forceinline__ u64 ceil_div(u64 a, u64 b) { return (a + b - 1) / b; }
 
+// Shared-memory layouts round every region's start up to 16 bytes, so that
+// any key or counter type may follow an element area of any size.
+constexpr size_t a16(size_t x) { return (x + 15) / 16 * 16; }
+
 __device__ __forceinline__ void set_status(ChunkCounters* c, u32 bits) { atomicOr(&c->status, bits); }
 
 // A failed bounds guard: the access is skipped, the chunk reports an

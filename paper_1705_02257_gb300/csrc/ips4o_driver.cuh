@@ -216,21 +216,23 @@ inline u32 leaves_for(u64 n, u64 base_cap, u32 k_max) {
 // leaves the planner gives that size (the class table, else leaves_for),
 // down to the recursion threshold.  When the last level's nominal buckets
 // come within a factor of 4 of the threshold, sampling may leave some above
-// it, and one more round is added; two more rounds take a level with more
-// subproblems than nominal and one level more than nominal (skewed keys,
-// such as Exponential's).  Rarer stragglers, and any deeper recursion, go to
-// the segment scheduler after the last round.
+// it, and one more round is added; two more rounds per nominal level (at
+// most four) take levels with more subproblems than nominal and levels more
+// than nominal (skewed keys, such as Exponential's); an empty round costs a
+// few microseconds of launches.  Rarer stragglers, and any deeper recursion,
+// go to the segment scheduler after the last round.
 inline u32 rounds_for(u64 n, u64 cap, u64 base_cap, u32 k_max, u32 max_sub) {
     double subs = 1.0, m = (double)n;
-    u32 r = 0;
+    u32 r = 0, levels = 0;
     while (m > (double)cap && r < 4096) {
+        ++levels;
         r += (u32)std::ceil(subs / (double)max_sub);
         const ips4o_class_params cp = class_table()[63 - __builtin_clzll((u64)m)];
         const u32 K = cp.leaves ? (u32)cp.leaves : leaves_for((u64)m, base_cap, k_max);
         subs *= K;
         m /= K;
     }
-    return r + 2 + (m * 4.0 > (double)cap ? 1u : 0u);
+    return r + std::min<u32>(2 * levels, 4) + (m * 4.0 > (double)cap ? 1u : 0u);
 }
 
 #define IPS4O_CUDA(call)                                    \

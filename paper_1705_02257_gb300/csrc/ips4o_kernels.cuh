@@ -96,18 +96,18 @@ struct ClassifyCfg {
     static constexpr int B = T::kBlock;
     static constexpr int MAXBLK = 352;                        // >= (256*(B-1) + TILE) / B
     static constexpr size_t off_buf = 0;
-    static constexpr size_t off_stage = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
-    static constexpr size_t off_tree = off_stage + (size_t)STAGES * TILE * sizeof(E);
-    static constexpr size_t off_spl = off_tree + kMaxLeaves * sizeof(K);
-    static constexpr size_t off_fill = off_spl + kMaxLeaves * sizeof(K);
-    static constexpr size_t off_cnt = off_fill + kMaxBuckets * 4;
-    static constexpr size_t off_off = off_cnt + kMaxBuckets * 4;
-    static constexpr size_t off_bscan = off_off + kMaxBuckets * 4;
-    static constexpr size_t off_total = off_bscan + kMaxBuckets * 4;
-    static constexpr size_t off_blkb = off_total + kMaxBuckets * 4;
-    static constexpr size_t off_emit = off_blkb + MAXBLK * 2;
-    static constexpr size_t off_misc = off_emit + kMaxBuckets * 2;
-    static constexpr size_t smem_bytes = off_misc + 64 * 8;
+    static constexpr size_t off_stage = a16(off_buf + (size_t)kMaxBuckets * B * sizeof(E));
+    static constexpr size_t off_tree = a16(off_stage + (size_t)STAGES * TILE * sizeof(E));
+    static constexpr size_t off_spl = a16(off_tree + kMaxLeaves * sizeof(K));
+    static constexpr size_t off_fill = a16(off_spl + kMaxLeaves * sizeof(K));
+    static constexpr size_t off_cnt = a16(off_fill + kMaxBuckets * 4);
+    static constexpr size_t off_off = a16(off_cnt + kMaxBuckets * 4);
+    static constexpr size_t off_bscan = a16(off_off + kMaxBuckets * 4);
+    static constexpr size_t off_total = a16(off_bscan + kMaxBuckets * 4);
+    static constexpr size_t off_blkb = a16(off_total + kMaxBuckets * 4);
+    static constexpr size_t off_emit = a16(off_blkb + MAXBLK * 2);
+    static constexpr size_t off_misc = a16(off_emit + kMaxBuckets * 2);
+    static constexpr size_t smem_bytes = a16(off_misc + 64 * 8);
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
     static_assert(MAXBLK < 65536 && TILE < (1 << 30), "packed scan fields");
     static_assert(TILE % TPB == 0, "tile must be a multiple of the CTA size");
@@ -132,19 +132,20 @@ struct ClassifyRegCfg {
     static constexpr int GRP = TILE + (PAD ? 2 * kMaxBuckets : 0);
     static constexpr int MAXBLK = 384;                         // >= (256*(B-1) + TILE) / B
     static constexpr size_t off_buf = 0;
-    static constexpr size_t off_grp = off_buf + (size_t)kMaxBuckets * B * sizeof(E);
-    static constexpr size_t off_tree = off_grp + (size_t)GRP * sizeof(E);
-    static constexpr size_t off_spl = off_tree + kMaxLeaves * sizeof(K);
-    static constexpr size_t off_fill = off_spl + (kMaxLeaves + 8) * sizeof(K);
-    static constexpr size_t off_cnt = off_fill + kMaxBuckets * 4;          // u32[2][kMaxBuckets]
-    static constexpr size_t off_total = off_cnt + 2 * kMaxBuckets * 4;
-    static constexpr size_t off_dst = off_total + kMaxBuckets * 4;
-    static constexpr size_t off_binfo = off_dst + kMaxBuckets * 4;         // uint2[2][kMaxBuckets]
-    static constexpr size_t off_desc = off_binfo + 2 * kMaxBuckets * 8;    // u32[2][MAXBLK]
-    static constexpr size_t off_misc = off_desc + 2 * MAXBLK * 4;         // u32[16]
-    static constexpr size_t off_lut = off_misc + 64;                       // u16[kLutCells + 8]
-    static constexpr size_t smem_bytes = off_lut + (kLutCells + 8) * 2;
-    static_assert(off_grp % 16 == 0 && off_buf == 0, "destinations count elements from the base");
+    static constexpr size_t off_grp = a16(off_buf + (size_t)kMaxBuckets * B * sizeof(E));
+    static constexpr size_t off_tree = a16(off_grp + (size_t)GRP * sizeof(E));
+    static constexpr size_t off_spl = a16(off_tree + kMaxLeaves * sizeof(K));
+    static constexpr size_t off_fill = a16(off_spl + (kMaxLeaves + 8) * sizeof(K));
+    static constexpr size_t off_cnt = a16(off_fill + kMaxBuckets * 4);          // u32[2][kMaxBuckets]
+    static constexpr size_t off_total = a16(off_cnt + 2 * kMaxBuckets * 4);
+    static constexpr size_t off_dst = a16(off_total + kMaxBuckets * 4);
+    static constexpr size_t off_binfo = a16(off_dst + kMaxBuckets * 4);         // uint2[2][kMaxBuckets]
+    static constexpr size_t off_desc = a16(off_binfo + 2 * kMaxBuckets * 8);    // u32[2][MAXBLK]
+    static constexpr size_t off_misc = a16(off_desc + 2 * MAXBLK * 4);         // u32[16]
+    static constexpr size_t off_lut = a16(off_misc + 64);                       // u16[kLutCells + 8]
+    static constexpr size_t smem_bytes = a16(off_lut + (kLutCells + 8) * 2);
+    static_assert(off_grp % 16 == 0 && off_grp % sizeof(E) == 0 && off_buf == 0,
+                  "destinations count elements from the base");
     static_assert((size_t)(256 * (B - 1) + TILE) / B <= (size_t)MAXBLK, "MAXBLK too small");
     static_assert(TILE % TPB == 0 && TPB >= kMaxBuckets, "tile must be a multiple of the CTA size");
     static_assert(kLutCells % TPB == 0 && (size_t)GRP * sizeof(E) >= kLutCells, "table build layout");
@@ -1074,12 +1075,12 @@ struct PermuteCfg {
     // block buffers of the warps, then one copy of the subproblem's tables
     // shared by the CTA (all its warps move blocks of the same subproblem)
     static constexpr size_t off_buf = 0;                                          // E[NW][2][V][B]
-    static constexpr size_t off_tree = off_buf + (size_t)NW * 2 * V * T::kBlock * sizeof(E);
-    static constexpr size_t off_spl = off_tree + (size_t)kMaxLeaves * sizeof(K);
-    static constexpr size_t off_delim = off_spl + (size_t)kMaxLeaves * sizeof(K);
-    static constexpr size_t off_gpre = off_delim + (size_t)(kMaxBuckets + 4) * 4;   // u16[1025]
-    static constexpr size_t off_misc = off_gpre + 1032 * 2;
-    static constexpr size_t smem_bytes = off_misc + 40 * 8;
+    static constexpr size_t off_tree = a16(off_buf + (size_t)NW * 2 * V * T::kBlock * sizeof(E));
+    static constexpr size_t off_spl = a16(off_tree + (size_t)kMaxLeaves * sizeof(K));
+    static constexpr size_t off_delim = a16(off_spl + (size_t)kMaxLeaves * sizeof(K));
+    static constexpr size_t off_gpre = a16(off_delim + (size_t)(kMaxBuckets + 4) * 4);   // u16[1025]
+    static constexpr size_t off_misc = a16(off_gpre + 1032 * 2);
+    static constexpr size_t smem_bytes = a16(off_misc + 40 * 8);
     static_assert(BB <= 512 && BB % CHB == 0, "a block is at most 512 bytes of whole chunks");
 };
 
@@ -1406,7 +1407,7 @@ struct CleanupCfg {
     static constexpr int WPC = TPB / 32;
     static constexpr int B = T::kBlock;
     static constexpr size_t off_ov = 0;                                 // E[WPC][B] overshoot per warp
-    static constexpr size_t smem_bytes = off_ov + (size_t)WPC * B * sizeof(E);
+    static constexpr size_t smem_bytes = a16(off_ov + (size_t)WPC * B * sizeof(E));
 };
 
 // Cleanup of bucket b of subproblem j by one warp (Section 4.3): its
@@ -1537,9 +1538,12 @@ struct CleanupCtaCfg {
     static constexpr int TPB = 256;
     static constexpr int B = T::kBlock;
     static constexpr size_t off_ov = 0;
-    static constexpr size_t off_lpre = off_ov + (size_t)B * sizeof(E);
-    static constexpr size_t off_src = off_lpre + (size_t)(kMaxStripesPerSub + 1) * 4 + 4;
-    static constexpr size_t smem_bytes = off_src + (size_t)kMaxStripesPerSub * 8;
+    static constexpr size_t off_lpre = a16(off_ov + (size_t)B * sizeof(E));
+    static constexpr size_t off_src = a16(off_lpre + (size_t)(kMaxStripesPerSub + 1) * 4 + 4);
+    static constexpr size_t smem_bytes = a16(off_src + (size_t)kMaxStripesPerSub * 8);
+    // 100-byte records leave B * sizeof(E) a multiple of 4 only: the tables
+    // after the block start on their own 16-byte boundary
+    static_assert(off_lpre % 16 == 0 && off_src % 16 == 0, "aligned tables");
 };
 
 // Cleanup of bucket b of subproblem j by the whole CTA (CleanupCtaCfg<T>::TPB
