@@ -265,13 +265,15 @@ def run_gpu(args):
         base_params["record_path"] = args.record_path
     if base_params:
         ips4o.set_params(**base_params)
+    # ips4o_sort, or the strictly in-place ips4o_sort_strict (Section 4.6)
+    sort_fn = ips4o.sort_strict if args.strict else ips4o.sort
 
     def one_step():
         work.copy_(pristine)
         torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        ips4o.sort(work, kt)
+        sort_fn(work, kt)
         e.record(stream)
         torch.cuda.synchronize()
         return s.elapsed_time(e)
@@ -318,7 +320,7 @@ def run_gpu(args):
     # algorithmic bytes per launch (Appendix B I/O volume): classification and
     # block permutation each read and write the elements of the launch once.
     # Records are distributed as 16-byte (key prefix, index) pairs.
-    rec_blocks = kt == "rec100" and args.record_path == 1        # records moved in place, not through pairs
+    rec_blocks = kt == "rec100" and (args.record_path == 1 or args.strict)   # records moved in place, not pairs
     dist_elem = 16 if kt == "rec100" and not rec_blocks else elem
     # elements classified over all levels of one sort (a deeper level often
     # holds only a few buckets): the classification and permutation volume
@@ -399,7 +401,8 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": DTYPE_NAME[kt], "data": "synthetic",
         "config": {"workload": f"{'sort' if kt == 'rec100' and not rec_blocks else 'in-place sort'} of 2^{args.log2n} "
                                f"{KT_LABEL[kt]}, {args.dist} (seed 1)"
-                               f"{' (in-place block path)' if rec_blocks else (' (key + index indirection)' if kt == 'rec100' else '')}",
+                               f"{' (in-place block path)' if rec_blocks else (' (key + index indirection)' if kt == 'rec100' else '')}"
+                               f"{', strictly in place (ips4o_sort_strict)' if args.strict else ''}",
                    "n": n, "key_type": kt, "distribution": args.dist,
                    "l2": f"input {n * elem / 2**30:.2f} GiB per step, larger than the 129 MB L2 (no flush needed)",
                    "parallelism": f"replicas x{world}", "levels": levels},
@@ -753,6 +756,8 @@ def main():
                     help="batched: tune leaves / alpha per size class first and sort with that table")
     ap.add_argument("--record-path", type=int, default=0, choices=[0, 1],
                     help="100-byte records: 0 key + index indirection (default), 1 in-place blocks")
+    ap.add_argument("--strict", action="store_true",
+                    help="plain workload: time ips4o_sort_strict (Section 4.6, workspace independent of n)")
     ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2],
                     help="batched: 0 automatic, 1 level by level, 2 one CTA per array")
     args = ap.parse_args()

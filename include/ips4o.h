@@ -105,6 +105,9 @@ typedef struct {
                                per record), 1 the records moved in place through the distribution
                                steps in blocks of 5 (not stable; workspace independent of the
                                record size but for the blocks) */
+    uint64_t strict_window; /* ips4o_sort_strict: elements scanned per pass of its bucket-head scan
+                               (rounded down to a multiple of 2048, at least 2048); 0 selects about
+                               256 MiB of elements */
 } ips4o_params;
 
 /* Parameters of the distribution steps per size class, as an autotuner picks
@@ -168,11 +171,32 @@ typedef struct {
  *     1, key_type, stream), a call allocates nothing and can be captured into
  *     a CUDA graph; under capture without a large enough reservation it
  *     returns IPS4O_ERR_TOO_LARGE and queues nothing.
- *   - Extra device memory (Theorem 2): a leftover pool for 4 stripes per SM
+ *   - Extra device memory (Theorem 2): a leftover pool for 2 stripes per SM
  *     (independent of n) plus per-chunk tables, two level queues of
  *     n / (base-case size) entries, and the segment scheduler's per-CTA
- *     areas; see ips4o_workspace_bytes. */
+ *     areas; see ips4o_workspace_bytes.  ips4o_sort_strict needs no queue. */
 ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream);
+
+/* Sort d_ptr[0..n) in place with extra memory independent of n: the strictly
+ * in-place recursion of Section 4.6.  Each distribution step moves the
+ * largest element of every bucket that must be distributed again to the
+ * bucket's first slot; the end of such a bucket is then the first later
+ * position holding a larger key, so the remaining work is found by scanning
+ * the array (a window of params.strict_window elements at a time) instead of
+ * being kept in queues.  Every key type, including 100-byte records (moved in
+ * place in blocks of 5, not through key + index pairs).  The result equals
+ * ips4o_sort's.
+ *   - Synchronous: the host waits on `stream` once per round of subproblems
+ *     and once per scanned window, and the call returns when the array is
+ *     sorted; device-side errors are returned by the call itself.  Refused
+ *     (IPS4O_ERR_INVALID_ARG) while the stream is being captured.
+ *   - Extra device memory: ips4o_workspace_bytes_strict(n, key_type), the
+ *     same for every n above the base case. */
+ips4o_status ips4o_sort_strict(void* d_ptr, size_t n, int key_type, void* stream);
+
+/* Device workspace in bytes that ips4o_sort_strict uses for n elements of
+ * key_type with the current parameters (host computation, no device work). */
+size_t ips4o_workspace_bytes_strict(size_t n, int key_type);
 
 /* Same as ips4o_sort but for an array in HOST memory: the elements are
  * brought to a device staging buffer (owned by the library and kept for

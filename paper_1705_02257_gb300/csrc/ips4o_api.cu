@@ -296,6 +296,54 @@ ips4o_status ips4o_sort(void* d_ptr, size_t n, int key_type, void* stream) {
     return dispatch(*st, d_ptr, n, key_type, (cudaStream_t)stream, nullptr);
 }
 
+ips4o_status ips4o_sort_strict(void* d_ptr, size_t n, int key_type, void* stream) {
+    ips4o_status rc = check_args(d_ptr, n, key_type);
+    if (rc != IPS4O_OK) return rc;
+    if (n < 2) return IPS4O_OK;
+    cudaError_t e;
+    DeviceState* st = stream_state(stream, &e);
+    if (!st) { set_last_cuda_error(e, "cudaGetDevice"); return IPS4O_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(st->mtx);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) { set_last_cuda_error(e, "cudaStreamIsCapturing"); return IPS4O_ERR_CUDA; }
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_last_message("ips4o_sort_strict synchronises between batches: not while the stream is being captured");
+        return IPS4O_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (key_type) {
+    case IPS4O_U64: rc = sort_strict_u64(*st, d_ptr, n, s); break;
+    case IPS4O_F64: rc = sort_strict_f64(*st, d_ptr, n, s); break;
+    case IPS4O_PAIR_U64: rc = sort_strict_pair(*st, d_ptr, n, s); break;
+    case IPS4O_QUARTET_U64: rc = sort_strict_quartet(*st, d_ptr, n, s); break;
+    case IPS4O_REC100_K10: rc = sort_strict_rec100(*st, d_ptr, n, s); break;
+    default: return IPS4O_ERR_UNSUPPORTED_TYPE;
+    }
+    publish_stats(*st);
+    if (rc != IPS4O_OK) {
+        st->pending = false;
+        return rc;
+    }
+    return finalize_pending(*st);
+}
+
+size_t ips4o_workspace_bytes_strict(size_t n, int key_type) {
+    int sms = 152;
+    cudaError_t e;
+    DeviceState* st = current_device_state(&e);
+    if (st) sms = st->sms;
+    else cudaGetLastError();
+    switch (key_type) {
+    case IPS4O_U64: return strict_workspace_bytes_u64(n, sms);
+    case IPS4O_F64: return strict_workspace_bytes_f64(n, sms);
+    case IPS4O_PAIR_U64: return strict_workspace_bytes_pair(n, sms);
+    case IPS4O_QUARTET_U64: return strict_workspace_bytes_quartet(n, sms);
+    case IPS4O_REC100_K10: return strict_workspace_bytes_rec100(n, sms);
+    default: return 0;
+    }
+}
+
 ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t num_segments, int key_type,
                                   void* stream) {
     if (key_type < 0 || key_type > IPS4O_QUARTET_U64 || elem_size(key_type) == 0) return IPS4O_ERR_UNSUPPORTED_TYPE;

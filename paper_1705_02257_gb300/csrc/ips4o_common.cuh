@@ -265,7 +265,21 @@ struct LoopState {
     u64 stripe_len;         // stripe length of the current level
     u64 blocks_moved, blocks_skipped, fix_blocks, base_buckets, elements_distributed, subproblems, chunks;
     u32 fallback_tasks;     // subproblems left to the segment scheduler after the last round
-    u32 pad;
+    u32 strict;             // 1: the strictly in-place recursion (buckets are marked, not queued)
+    u32 marks;              // strict: buckets marked by the current batch
+    u32 carry_desc;         // strict: the piece that reaches past the scanned window holds a descent
+    u64 batch_begin;        // strict: first element of the current batch's subproblems
+    u64 scan_pos, scan_end; // strict: the window [scan_pos, scan_end) of the current scan pass
+    u64 carry_head;         // strict: head of the piece that reaches past the window (kNoHead: none)
+};
+
+constexpr u64 kNoHead = ~0ull;
+
+// Summary of one tile of the strict recursion's bucket-head scan.
+struct ScanTile {
+    u64 first_head, last_head;   // absolute positions of the tile's first and last head (kNoHead: none)
+    u32 desc_first;              // a descent before the first head (the whole tile when it has none)
+    u32 desc_last;               // a descent after the last head
 };
 
 // Pointers into the workspace for one key type.
@@ -301,8 +315,10 @@ struct Workspace {
     ChunkCounters* ctr;       // [1]
     Task* next_tasks2;        // [next_cap]      the second level queue of the device-planned recursion
     LoopState* ls;            // [1] device-planned recursion; null when the host plans the levels
+    key_t* scan_max;          // [scan_cap] strict recursion: largest key per scan tile, then the prefix before it
+    ScanTile* scan_tiles;     // [scan_cap] strict recursion: heads and descents per scan tile
     u32 max_sub, max_stripes;
-    u64 pool_cap, next_cap, init_cap, stack_cap;
+    u64 pool_cap, next_cap, init_cap, stack_cap, scan_cap;
 };
 
 // ------------------------------------------------------------ primitives

@@ -16,7 +16,7 @@
 
 #include "ips4o_host.h"
 #include "ips4o_kernels.cuh"
-#include "ips4o_rounds.cuh"
+#include "ips4o_strict.cuh"
 
 namespace ips4o {
 
@@ -43,6 +43,7 @@ struct Caps {
     u64 stack_cap;      // segment scheduler: buckets per CTA stack (0 = not used)
     u32 stack_slots = 0;   // segment scheduler: CTA stacks
     bool rounds = false;   // device-planned levels: a second task queue and the loop state
+    u64 scan_cap = 0;      // strict recursion: tiles of one scan window
 };
 
 constexpr u64 kSegStackCap = 2048;     // per CTA; a distribution step pushes at most 256 buckets
@@ -116,6 +117,30 @@ Caps<T> caps_for_rounds(u64 n, int sms, u64 cap) {
     return c;
 }
 
+// Elements of one window of the strict recursion's scan: about 256 MiB, a
+// whole number of scan tiles; params.strict_window overrides it.
+template <class T>
+u64 strict_window(const ips4o_params& p) {
+    typedef typename T::elem_t E;
+    u64 w = p.strict_window ? (u64)p.strict_window : kScanWindowBytes / sizeof(E);
+    w = std::max<u64>(kScanTile, w / kScanTile * kScanTile);
+    return w;
+}
+
+// Workspace of the strict recursion: the rounds' (whose chunk limits do not
+// depend on n) with a subproblem list for one window and the scan tiles;
+// no level queues and no segment scheduler, so nothing grows with n.
+template <class T>
+Caps<T> caps_for_strict(u64 n, int sms, u64 cap, u64 window) {
+    Caps<T> c = caps_for_rounds<T>(std::min<u64>(n, window), sms, cap);
+    c.next_cap = window / (cap + 1) + 64;
+    c.init_cap = 0;
+    c.stack_cap = 0;
+    c.stack_slots = 0;
+    c.scan_cap = (window + kScanTile - 1) / kScanTile;
+    return c;
+}
+
 // CTAs of the segment scheduler that finishes a device-planned sort.
 template <class T>
 u32 fallback_grid(const Caps<T>& c) {
@@ -166,6 +191,8 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.next_tasks2 = c.rounds ? (Task*)take(c.next_cap * sizeof(Task)) : nullptr;
     w.ls = c.rounds ? (LoopState*)take(sizeof(LoopState)) : nullptr;
+    w.scan_max = c.scan_cap ? (K*)take(c.scan_cap * sizeof(K)) : nullptr;
+    w.scan_tiles = c.scan_cap ? (ScanTile*)take(c.scan_cap * sizeof(ScanTile)) : nullptr;
     if (!base) {
         w.next_tasks2 = nullptr;
         w.ls = nullptr;
@@ -176,6 +203,7 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.next_cap = c.next_cap;
     w.init_cap = c.init_cap;
     w.stack_cap = c.stack_cap;
+    w.scan_cap = c.scan_cap;
     if (ws) *ws = w;
     return align_up(off, 256);
 }
@@ -622,6 +650,142 @@ struct Driver {
         return levels(d, std::vector<Task>{Task{0, n}}, part);
     }
 
+    // One round of the device-planned recursion: k_plan picks the chunk, the
+    // distribution step runs it (reading src, writing d), the base case sorts
+    // the small buckets it made; with mark, the larger buckets get their
+    // largest element in front (the strict recursion).
+    ips4o_status launch_round(E* d, const E* src, const PlanArgs& pa, bool mark) {
+        const u32 sms = (u32)st.sms;
+        IPS4O_LAUNCH(7, (k_plan<T><<<1, 1024, 0, stream>>>(ws, pa)));
+        IPS4O_LAUNCH(0, (k_sample<T, 512><<<2 * sms, 512, 0, stream>>>(src, ws, 0, prm.seed)));
+        IPS4O_LAUNCH(1, (k_classify<T><<<sms, ClassifyRegCfg<T>::TPB, ClassifyRegCfg<T>::smem_bytes, stream>>>(
+                            d, src, ws, 0)));
+        IPS4O_LAUNCH(2, (k_prefix<T, 256><<<4 * sms, 256, 0, stream>>>(ws, 0)));
+        IPS4O_LAUNCH(3, (k_fix<T, 256><<<2 * sms, 256, 0, stream>>>(d, ws)));
+        IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
+                            d, ws, 0, spin_limit())));
+        IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<2 * sms, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
+                                            stream>>>(d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
+        IPS4O_LAUNCH(5, (k_cleanup<T><<<8 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
+                            d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
+        if (mark) IPS4O_LAUNCH(5, (k_mark<T, 512><<<2 * sms, 512, 0, stream>>>(d, ws, rec_cap)));
+        return launch_base_lists(d);
+    }
+
+    // A sort that is one base case, with the loop state of the device-planned
+    // recursion (statistics are read from it).
+    ips4o_status launch_base_only(E* d, u64 n) {
+        IPS4O_LAUNCH(7, (k_plan_base<T><<<1, 32, 0, stream>>>(ws, n)));
+        if (n <= (u64)T::kBaseTiny) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<1, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                                d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+        } else if (n <= (u64)T::kBaseSmall) {
+            IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                                d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+        } else {
+            IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<1, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                                d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+        }
+        IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+        return IPS4O_OK;
+    }
+
+    // The base case of the buckets in the three base lists.
+    ips4o_status launch_base_lists(E* d) {
+        const u32 sms = (u32)st.sms;
+        IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                            d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+        IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<2 * sms, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                            d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+        IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                            d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+        return IPS4O_OK;
+    }
+
+    // The strictly in-place sort (Section 4.6, see ips4o_strict.cuh): the
+    // host loop over batches of subproblems found by scanning the array; the
+    // only state between batches is the array, the scan position and the
+    // piece carried across a window edge.  Synchronises once per round and
+    // once per scanned window; statistics and device-side errors are read by
+    // finalize_pending (the caller's).
+    ips4o_status run_strict(E* d, u64 n) {
+        const u64 rc_cap = recursion_cap<T>(prm);
+        const u64 window = strict_window<T>(prm);
+        const Caps<T> c = n <= rc_cap ? caps_for_rounds<T>(n, st.sms, rc_cap)
+                                      : caps_for_strict<T>(n, st.sms, rc_cap, window);
+        ips4o_status rc = setup(n, 0, &c, kGrow);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = n;
+        st.d_status = &ws.ls->status;
+        st.pending = true;
+        st.pending_ls = ws.ls;
+        st.pending_stream = stream;
+        if (n <= rc_cap) return launch_base_only(d, n);      // one base case: nothing recurses
+        static_assert(sizeof(LoopState) <= 64 * sizeof(Task), "loop state read back through the task staging");
+        LoopState* h_ls = (LoopState*)h_tasks;
+        auto read_ls = [&]() -> ips4o_status {
+            IPS4O_CUDA(cudaMemcpyAsync(h_ls, ws.ls, sizeof(LoopState), cudaMemcpyDeviceToHost, stream));
+            IPS4O_CUDA(cudaStreamSynchronize(stream));
+            return IPS4O_OK;
+        };
+        const u32 sms = (u32)st.sms;
+        IPS4O_LAUNCH(7, (k_strict_init<T><<<1, 32, 0, stream>>>(ws, n)));
+        PlanArgs pa{};
+        pa.n = n;
+        pa.k_max = k_max;
+        pa.alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
+        pa.base_cap = base_cap;
+        pa.sms = sms;
+        pa.w0 = (u32)std::max(1, prm.stripes_per_sm);
+        const u32 scan_grid = (u32)std::min<u64>((window + kScanTile - 1) / kScanTile, 4ull * sms);
+        // every batch makes progress (a subproblem that is not all equal is
+        // split into smaller pieces, with a new sample each batch); a batch
+        // that repeats the previous one's first subproblem, count and size
+        // many times over means a bug, reported instead of looping
+        u64 last_begin = ~0ull, last_elems = 0, last_delta = ~0ull;
+        u32 last_count = 0, repeats = 0;
+        for (u32 batch = 0;; ++batch) {
+            pa.newlevel = 1;
+            pa.level = batch;
+            for (;;) {                                     // the rounds of the batch
+                if ((rc = launch_round(d, d, pa, true)) != IPS4O_OK) return rc;
+                pa.newlevel = 0;
+                if ((rc = read_ls()) != IPS4O_OK) return rc;
+                if (h_ls->status || h_ls->cur_pos >= h_ls->cur_count) break;
+            }
+            if (h_ls->status) break;
+            bool done = false;
+            for (;;) {                                     // scan windows until work is found
+                IPS4O_LAUNCH(7, (k_scan_begin<T><<<1, 32, 0, stream>>>(ws, n, window)));
+                IPS4O_LAUNCH(7, (k_scan_max<T><<<scan_grid, kScanTPB, 0, stream>>>(d, ws)));
+                IPS4O_LAUNCH(7, (k_scan_prefix<T><<<1, 1024, 0, stream>>>(d, ws)));
+                IPS4O_LAUNCH(7, (k_scan_heads<T><<<scan_grid, kScanTPB, 0, stream>>>(d, ws, (u32)rc_cap)));
+                IPS4O_LAUNCH(7, (k_scan_link<T><<<1, 1024, 0, stream>>>(ws, n, (u32)rc_cap)));
+                if ((rc = launch_base_lists(d)) != IPS4O_OK) return rc;
+                if ((rc = read_ls()) != IPS4O_OK) return rc;
+                if (h_ls->status || h_ls->cur_count > 0) break;
+                if (h_ls->scan_pos >= n) {
+                    done = true;
+                    break;
+                }
+            }
+            if (done || h_ls->status) break;
+            const u64 elems = h_ls->elements_distributed, delta = elems - last_elems;
+            const bool same = h_ls->batch_begin == last_begin && h_ls->cur_count == last_count && delta == last_delta;
+            repeats = same ? repeats + 1 : 0;
+            if (repeats >= 64) {
+                set_last_message("strict recursion: a batch repeated without progress");
+                return IPS4O_ERR_INTERNAL;
+            }
+            last_begin = h_ls->batch_begin;
+            last_count = h_ls->cur_count;
+            last_elems = elems;
+            last_delta = delta;
+        }
+        IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+        return IPS4O_OK;
+    }
+
     // The sort as enqueued work only (Section 4's recursion planned on the
     // device, see ips4o_rounds.cuh): no host synchronisation, so the call
     // returns at once and can be captured in a CUDA graph.  Under capture
@@ -641,20 +805,10 @@ struct Driver {
         if (!from) from = d;
         if (n <= (u64)rec_cap) {
             if (from != d) IPS4O_CUDA(cudaMemcpyAsync(d, from, n * sizeof(E), cudaMemcpyDefault, stream));
-            IPS4O_LAUNCH(7, (k_plan_base<T><<<1, 32, 0, stream>>>(ws, n)));
-            if (n <= (u64)T::kBaseTiny) {
-                IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<1, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
-                                    d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
-            } else if (n <= (u64)T::kBaseSmall) {
-                IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
-                                    d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
-            } else {
-                IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<1, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
-                                    d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
-            }
-            IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+            rc = launch_base_only(d, n);
+            if (rc != IPS4O_OK) return rc;
         } else {
-            PlanArgs pa;
+            PlanArgs pa{};
             pa.n = n;
             pa.first = 1;
             pa.k_max = k_max;
@@ -666,25 +820,8 @@ struct Driver {
             const u32 sms = (u32)st.sms;
             for (u32 r = 0; r < R; ++r) {
                 pa.first = r == 0 ? 1u : 0u;
-                const E* src = r == 0 ? from : d;     // round 0 is the whole input (level 1)
-                IPS4O_LAUNCH(7, (k_plan<T><<<1, 1024, 0, stream>>>(ws, pa)));
-                IPS4O_LAUNCH(0, (k_sample<T, 512><<<2 * sms, 512, 0, stream>>>(src, ws, 0, prm.seed)));
-                IPS4O_LAUNCH(1, (k_classify<T><<<sms, ClassifyRegCfg<T>::TPB, ClassifyRegCfg<T>::smem_bytes, stream>>>(
-                                    d, src, ws, 0)));
-                IPS4O_LAUNCH(2, (k_prefix<T, 256><<<4 * sms, 256, 0, stream>>>(ws, 0)));
-                IPS4O_LAUNCH(3, (k_fix<T, 256><<<2 * sms, 256, 0, stream>>>(d, ws)));
-                IPS4O_LAUNCH(4, (k_permute<T><<<permute_grid, PermuteCfg<T>::TPB, PermuteCfg<T>::smem_bytes, stream>>>(
-                                    d, ws, 0, spin_limit())));
-                IPS4O_LAUNCH(5, (k_cleanup_cta<T><<<2 * sms, CleanupCtaCfg<T>::TPB, CleanupCtaCfg<T>::smem_bytes,
-                                                    stream>>>(d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
-                IPS4O_LAUNCH(5, (k_cleanup<T><<<8 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
-                                    d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
-                IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
-                                    d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
-                IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<2 * sms, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
-                                    d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
-                IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
-                                    d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+                rc = launch_round(d, r == 0 ? from : d, pa, false);   // round 0 is the whole input (level 1)
+                if (rc != IPS4O_OK) return rc;
             }
             // subproblems left after the last round: the segment scheduler
             IPS4O_LAUNCH(7, (k_rounds_done<T><<<1, 1024, 0, stream>>>(ws)));
@@ -897,6 +1034,24 @@ template <class T>
 ips4o_status sort_from_t(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s) {
     Driver<T> drv(st, s);
     return drv.enqueue_sort((typename T::elem_t*)d, (u64)n, (const typename T::elem_t*)src);
+}
+
+// The strictly in-place sort of d[0, n) (Section 4.6); returns when the
+// work is enqueued and its last batch found, the caller finalizes.
+template <class T>
+ips4o_status strict_sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    Driver<T> drv(st, s);
+    return drv.run_strict((typename T::elem_t*)d, (u64)n);
+}
+
+// Device workspace of a strict sort of n elements: for n above the base case
+// the same for every n.
+template <class T>
+size_t strict_workspace_bytes_t(size_t n, int sms) {
+    const ips4o_params& prm = global_params();
+    const u64 cap = recursion_cap<T>(prm);
+    const Caps<T> c = n <= cap ? caps_for_rounds<T>(n, sms, cap) : caps_for_strict<T>(n, sms, cap, strict_window<T>(prm));
+    return carve<T>(c, nullptr, nullptr);
 }
 
 // Grow the stream's workspace and staging to what a call on n elements in

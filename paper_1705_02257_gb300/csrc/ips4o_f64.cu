@@ -25,4 +25,8 @@ ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments) {
     return reserve_t<TF64>(st, n, num_segments);
 }
 size_t workspace_bytes_f64(size_t n, int sms) { return workspace_bytes_t<TF64>(n, sms); }
+ips4o_status sort_strict_f64(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    return strict_sort_t<TF64>(st, d, n, s);
+}
+size_t strict_workspace_bytes_f64(size_t n, int sms) { return strict_workspace_bytes_t<TF64>(n, sms); }
 }  // namespace ips4o

@@ -49,7 +49,7 @@ ips4o_status finalize_pending(DeviceState& st);
 ips4o_status collect_profile_events(DeviceState& st);
 
 // The library's default parameters (what ips4o_set_params(NULL) restores).
-constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0, 0};
+constexpr ips4o_params kDefaultParams = {256, 0, 0, 1, 0, 0x2545F4914F6CDD1Dull, 0, 0, 0, 0};
 
 DeviceState* stream_state(void* stream, cudaError_t* err);   // state of (current device, stream)
 DeviceState* current_device_state(cudaError_t* err);          // state of (current device, NULL stream)
@@ -111,6 +111,17 @@ size_t workspace_bytes_quartet(size_t n, int sms);
 ips4o_status sort_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s);
 size_t rec100_aux_bytes(size_t n);
 size_t workspace_bytes_u64(size_t n, int sms);
+// the strictly in-place sort (Section 4.6) per element type, and its workspace
+ips4o_status sort_strict_u64(DeviceState& st, void* d, size_t n, cudaStream_t s);
+ips4o_status sort_strict_f64(DeviceState& st, void* d, size_t n, cudaStream_t s);
+ips4o_status sort_strict_pair(DeviceState& st, void* d, size_t n, cudaStream_t s);
+ips4o_status sort_strict_quartet(DeviceState& st, void* d, size_t n, cudaStream_t s);
+ips4o_status sort_strict_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s);
+size_t strict_workspace_bytes_u64(size_t n, int sms);
+size_t strict_workspace_bytes_f64(size_t n, int sms);
+size_t strict_workspace_bytes_pair(size_t n, int sms);
+size_t strict_workspace_bytes_quartet(size_t n, int sms);
+size_t strict_workspace_bytes_rec100(size_t n, int sms);
 size_t workspace_bytes_f64(size_t n, int sms);
 size_t workspace_bytes_pair(size_t n, int sms);
 

@@ -1377,6 +1377,7 @@ template <class T>
 __device__ __forceinline__ void emit_bucket(const Workspace<T>& ws, Task task, u32 rec_cap) {
     const u64 size = task.n;
     if (size > (u64)rec_cap) {
+        if (ws.ls && ws.ls->strict) return;       // marked by k_mark and found again by the scan
         if (ws.ls) {
             const u32 idx = atomicAdd(&ws.ls->next_count, 1u);
             if (idx < ws.next_cap) ws.ls->next_q[idx] = task;

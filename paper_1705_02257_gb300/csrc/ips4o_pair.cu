@@ -25,4 +25,8 @@ ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments) {
     return reserve_t<TPair>(st, n, num_segments);
 }
 size_t workspace_bytes_pair(size_t n, int sms) { return workspace_bytes_t<TPair>(n, sms); }
+ips4o_status sort_strict_pair(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    return strict_sort_t<TPair>(st, d, n, s);
+}
+size_t strict_workspace_bytes_pair(size_t n, int sms) { return strict_workspace_bytes_t<TPair>(n, sms); }
 }  // namespace ips4o

@@ -23,4 +23,8 @@ ips4o_status reserve_quartet(DeviceState& st, size_t n, size_t num_segments) {
     return reserve_t<TQuartet>(st, n, num_segments);
 }
 size_t workspace_bytes_quartet(size_t n, int sms) { return workspace_bytes_t<TQuartet>(n, sms); }
+ips4o_status sort_strict_quartet(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    return strict_sort_t<TQuartet>(st, d, n, s);
+}
+size_t strict_workspace_bytes_quartet(size_t n, int sms) { return strict_workspace_bytes_t<TQuartet>(n, sms); }
 }  // namespace ips4o

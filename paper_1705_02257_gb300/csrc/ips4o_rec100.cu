@@ -88,6 +88,12 @@ static size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 size_t rec100_aux_bytes(size_t n) { return align256(n * (16 + kRecBytes)) + 2 * (n / 2 + 1) * 8 + 256; }
 
 // The block path: the records sorted in place by the distribution steps.
+// The records moved in place by the strictly in-place recursion (Section 4.6).
+ips4o_status sort_strict_rec100(DeviceState& st, void* d, size_t n, cudaStream_t s) {
+    return strict_sort_t<TRec>(st, d, n, s);
+}
+size_t strict_workspace_bytes_rec100(size_t n, int sms) { return strict_workspace_bytes_t<TRec>(n, sms); }
+
 static ips4o_status sort_rec100_blocks(DeviceState& st, void* d, size_t n, cudaStream_t s) {
     Driver<TRec> drv(st, s);
     return drv.run((RecElem*)d, (u64)n, nullptr);

@@ -30,6 +30,8 @@ struct PlanArgs {
     u32 base_cap;       // base-case class the adaptive number of leaves aims at (half of it per bucket)
     u32 sms;            // SMs: stripes should fill whole waves of them
     u32 w0;             // fewest stripes per SM tried for a level
+    u32 newlevel;       // strict recursion: this round starts a batch (planned like a new level)
+    u32 level;          // strict recursion: the batch's number (the sampling seed depends on it)
 };
 
 // Stripes of a subproblem of n elements for the level's stripe length len:
@@ -96,7 +98,8 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
         } else {
             fold_counters(ls, ws.ctr);
         }
-        s_newlevel = pa.first;
+        s_newlevel = pa.first | pa.newlevel;
+        if (pa.newlevel) ls->level = pa.level;
         if (ls->next_count > ws.next_cap) ls->status |= kStatusCapacity;   // (cannot happen: buckets are disjoint)
         if (!pa.first && ls->status == 0 && ls->cur_pos >= ls->cur_count && ls->next_count > 0) {
             Task* t = ls->cur_q;

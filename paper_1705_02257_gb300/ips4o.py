@@ -47,7 +47,8 @@ class Ips4oError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_int), ("alpha", ctypes.c_int), ("base_case_max", ctypes.c_int),
                 ("stripes_per_sm", ctypes.c_int), ("profile", ctypes.c_int), ("seed", ctypes.c_uint64),
-                ("segment_scheduler", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("record_path", ctypes.c_int)]
+                ("segment_scheduler", ctypes.c_int), ("spin_limit", ctypes.c_uint32), ("record_path", ctypes.c_int),
+                ("strict_window", ctypes.c_uint64)]
 
 
 class ClassParams(ctypes.Structure):
@@ -79,6 +80,10 @@ def _load():
     vp, sz, i32, u64p = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)
     lib.ips4o_sort.restype = i32
     lib.ips4o_sort.argtypes = [vp, sz, i32, vp]
+    lib.ips4o_sort_strict.restype = i32
+    lib.ips4o_sort_strict.argtypes = [vp, sz, i32, vp]
+    lib.ips4o_workspace_bytes_strict.restype = sz
+    lib.ips4o_workspace_bytes_strict.argtypes = [sz, i32]
     lib.ips4o_sort_host.restype = i32
     lib.ips4o_sort_host.argtypes = [vp, sz, i32, vp]
     lib.ips4o_sort_noalloc.restype = i32
@@ -131,6 +136,14 @@ def lib():
 # ------------------------------------------------------ C ABI, same names
 def ips4o_sort(d_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
     return _lib.ips4o_sort(d_ptr, n, key_type, stream)
+
+
+def ips4o_sort_strict(d_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
+    return _lib.ips4o_sort_strict(d_ptr, n, key_type, stream)
+
+
+def ips4o_workspace_bytes_strict(n: int, key_type: int) -> int:
+    return _lib.ips4o_workspace_bytes_strict(n, key_type)
 
 
 def ips4o_sort_host(h_ptr: int, n: int, key_type: int, stream: int = 0) -> int:
@@ -278,6 +291,23 @@ def sort(t, key_type="u64", stream: int | None = None):
     if rc:
         raise Ips4oError(rc, "ips4o_sort")
     return t
+
+
+def sort_strict(t, key_type="u64", stream: int | None = None):
+    """Sort a contiguous CUDA tensor in place with extra memory independent
+    of its size (Section 4.6); returns when the tensor is sorted."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    kt = _kt(key_type)
+    n = _count(t, kt)
+    rc = ips4o_sort_strict(t.data_ptr(), n, kt, _stream_of(t) if stream is None else stream)
+    if rc:
+        raise Ips4oError(rc, "ips4o_sort_strict")
+    return t
+
+
+def workspace_bytes_strict(n: int, key_type="u64") -> int:
+    return ips4o_workspace_bytes_strict(n, _kt(key_type))
 
 
 def sort_segmented(t, offsets, key_type="u64", stream: int | None = None):

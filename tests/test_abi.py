@@ -77,6 +77,21 @@ def test_class_params_validation(lib):
     assert ips4o.ips4o_get_class_params() == before            # rejected tables change nothing
 
 
+def test_strict_workspace_is_independent_of_n(lib):
+    """Section 4.6: the strictly in-place sort keeps no list whose length
+    depends on n, so its workspace is the same for every n above the base
+    case (host computation, no GPU needed)."""
+    lib.ips4o_workspace_bytes_strict.restype = ctypes.c_size_t
+    lib.ips4o_workspace_bytes_strict.argtypes = [ctypes.c_size_t, ctypes.c_int]
+    for kt in (0, 1, 2, 3, 4):
+        w = [lib.ips4o_workspace_bytes_strict(1 << k, kt) for k in (27, 28, 30, 33)]
+        assert len(set(w)) == 1 and w[0] > 0, (kt, w)
+        # and no larger than the device-planned sort's at 2^28 (u64, f64, pair,
+        # quartet; records there go through key + index pairs)
+        if kt != 3:
+            assert w[0] <= lib.ips4o_workspace_bytes(1 << 28, kt), (kt, w[0])
+
+
 def test_workspace_is_sublinear_in_n(lib):
     """Theorem 2: the extra space of the sort is O(k b t + log_k(n / n0)).
     Here t is a fixed number of stripes per SM, so the leftover pool and the
