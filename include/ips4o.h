@@ -107,7 +107,7 @@ typedef struct {
                                record size but for the blocks) */
     uint64_t strict_window; /* ips4o_sort_strict: elements scanned per pass of its bucket-head scan
                                (rounded down to a multiple of 2048, at least 2048); 0 selects about
-                               256 MiB of elements */
+                               1 GiB of elements */
 } ips4o_params;
 
 /* Parameters of the distribution steps per size class, as an autotuner picks

@@ -280,6 +280,8 @@ struct ScanTile {
     u64 first_head, last_head;   // absolute positions of the tile's first and last head (kNoHead: none)
     u32 desc_first;              // a descent before the first head (the whole tile when it has none)
     u32 desc_last;               // a descent after the last head
+    u32 next_head_tile;          // the first tile at or after this one with a head (tile count: none)
+    u32 desc_before;             // tiles before this one whose desc_first is set
 };
 
 // Pointers into the workspace for one key type.

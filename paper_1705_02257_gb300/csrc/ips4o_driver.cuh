@@ -117,7 +117,7 @@ Caps<T> caps_for_rounds(u64 n, int sms, u64 cap) {
     return c;
 }
 
-// Elements of one window of the strict recursion's scan: about 256 MiB, a
+// Elements of one window of the strict recursion's scan: about 1 GiB, a
 // whole number of scan tiles; params.strict_window overrides it.
 template <class T>
 u64 strict_window(const ips4o_params& p) {
@@ -668,7 +668,7 @@ struct Driver {
                                             stream>>>(d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
         IPS4O_LAUNCH(5, (k_cleanup<T><<<8 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
                             d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
-        if (mark) IPS4O_LAUNCH(5, (k_mark<T, 512><<<2 * sms, 512, 0, stream>>>(d, ws, rec_cap)));
+        if (mark) IPS4O_LAUNCH(5, (k_mark<T, 512><<<4 * sms, 512, 0, stream>>>(d, ws, rec_cap)));
         return launch_base_lists(d);
     }
 
@@ -737,7 +737,7 @@ struct Driver {
         pa.base_cap = base_cap;
         pa.sms = sms;
         pa.w0 = (u32)std::max(1, prm.stripes_per_sm);
-        const u32 scan_grid = (u32)std::min<u64>((window + kScanTile - 1) / kScanTile, 4ull * sms);
+        const u32 scan_grid = (u32)std::min<u64>((window + kScanTile - 1) / kScanTile, 8ull * sms);
         // every batch makes progress (a subproblem that is not all equal is
         // split into smaller pieces, with a new sample each batch); a batch
         // that repeats the previous one's first subproblem, count and size

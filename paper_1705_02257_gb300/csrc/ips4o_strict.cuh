@@ -31,36 +31,52 @@ namespace ips4o {
 constexpr u32 kScanTPB = 256;
 constexpr u32 kScanIPT = 8;
 constexpr u32 kScanTile = kScanTPB * kScanIPT;      // elements per tile of the head scan
-constexpr u64 kScanWindowBytes = 256ull << 20;      // default window: 256 MiB of elements
+constexpr u64 kScanWindowBytes = 1ull << 30;        // default window: 1 GiB of elements
+
+// Warp shuffle up of a key of any of the element types' key types.
+__device__ __forceinline__ u64 shfl_up_key(u64 v, int o) { return __shfl_up_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ QKey shfl_up_key(const QKey& v, int o) {
+    return QKey{__shfl_up_sync(0xffffffffu, v.a, o), __shfl_up_sync(0xffffffffu, v.b, o),
+                __shfl_up_sync(0xffffffffu, v.c, o)};
+}
+__device__ __forceinline__ RKey shfl_up_key(const RKey& v, int o) {
+    return RKey{__shfl_up_sync(0xffffffffu, v.hi, o), __shfl_up_sync(0xffffffffu, v.lo, o)};
+}
 
 // Block-wide exclusive prefix maximum of (v, has) over the threads of a CTA
-// of TPB threads; has = false stands for "no key" (below every key).
+// of TPB threads; has = false stands for "no key" (below every key).  Warp
+// scans by shuffles, then the warps' totals (s_k, s_h: TPB / 32 entries).
 template <class K, int TPB>
 __device__ __forceinline__ void block_excl_max(K v, bool has, K* s_k, u32* s_h, K* out, bool* out_has) {
-    const int tid = threadIdx.x;
-    K cur = v;
-    bool ch = has;
-    s_k[tid] = cur;
-    s_h[tid] = ch;
-    __syncthreads();
-    for (int off = 1; off < TPB; off <<= 1) {
-        K a = cur;
-        bool ah = false;
-        if (tid >= off) {
-            a = s_k[tid - off];
-            ah = s_h[tid - off] != 0;
+    constexpr int NW = TPB / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    K inc = v;
+    bool ih = has;
+    for (int o = 1; o < 32; o <<= 1) {
+        const K a = shfl_up_key(inc, o);
+        const bool ah = __shfl_up_sync(0xffffffffu, (u32)ih, o) != 0;
+        if (lane >= o && ah && (!ih || inc < a)) {
+            inc = a;
+            ih = true;
         }
-        __syncthreads();
-        if (ah && (!ch || cur < a)) {
-            cur = a;
-            ch = true;
-        }
-        s_k[tid] = cur;
-        s_h[tid] = ch;
-        __syncthreads();
     }
-    *out_has = tid > 0 && s_h[tid - 1] != 0;
-    if (*out_has) *out = s_k[tid - 1];
+    if (lane == 31) {
+        s_k[warp] = inc;
+        s_h[warp] = ih;
+    }
+    // the lane's exclusive value within the warp
+    K ex = shfl_up_key(inc, 1);
+    bool eh = __shfl_up_sync(0xffffffffu, (u32)ih, 1) != 0 && lane > 0;
+    __syncthreads();
+    for (int w = 0; w < NW; ++w) {
+        if (w >= warp) break;
+        if (s_h[w] && (!eh || ex < s_k[w])) {
+            ex = s_k[w];
+            eh = true;
+        }
+    }
+    *out = ex;
+    *out_has = eh;
     __syncthreads();
 }
 
@@ -136,7 +152,7 @@ template <class T, int TPB>
 __global__ void __launch_bounds__(TPB) k_mark(typename T::elem_t* arr, Workspace<T> ws, u32 rec_cap) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
-    constexpr int U = 4;
+    constexpr int U = sizeof(K) <= 8 ? 8 : 4;       // independent loads in flight per thread
     __shared__ K s_k[TPB / 32];
     __shared__ u32 s_h[TPB / 32];
     __shared__ u64 s_p[TPB / 32];
@@ -231,15 +247,18 @@ __global__ void __launch_bounds__(kScanTPB) k_scan_max(const typename T::elem_t*
     for (u64 t = blockIdx.x; t < nt; t += gridDim.x) {
         const u64 base = s + t * kScanTile;
         const u32 len = (u32)(e - base < kScanTile ? e - base : kScanTile);
+        K k[kScanIPT];
+#pragma unroll
+        for (u32 q = 0; q < kScanIPT; ++q)
+            if (threadIdx.x + q * kScanTPB < len) k[q] = T::key(arr[base + threadIdx.x + q * kScanTPB]);
         K m = key_min<K>();
         bool has = false;
-        for (u32 i = threadIdx.x; i < len; i += kScanTPB) {
-            const K k = T::key(arr[base + i]);
-            if (!has || m < k) {
-                m = k;
+#pragma unroll
+        for (u32 q = 0; q < kScanIPT; ++q)
+            if (threadIdx.x + q * kScanTPB < len && (!has || m < k[q])) {
+                m = k[q];
                 has = true;
             }
-        }
         K bm;
         bool bh;
         block_max<K, kScanTPB>(m, has, s_k, s_h, &bm, &bh);
@@ -392,20 +411,55 @@ __global__ void __launch_bounds__(kScanTPB) k_scan_heads(const typename T::elem_
 
 // Pieces that cross tiles (one CTA of 1024 threads): each starts at the last
 // head of a tile (or is the piece carried into the window) and ends at the
-// first head of a later tile; the tiles in between have no head.  The piece
-// that reaches the end of the window is carried into the next one, or ends
-// at n.
+// first head of a later tile; the tiles in between have no head.  Two scans
+// over the tiles give every tile the next tile with a head and the number of
+// earlier tiles with a descent before their first head, so each piece's end
+// and descent are found in constant time.  The piece that reaches the end of
+// the window is carried into the next one, or ends at n.
 template <class T>
 __global__ void __launch_bounds__(1024) k_scan_link(Workspace<T> ws, u64 n, u32 rec_cap) {
+    constexpr int TPB = 1024;
+    __shared__ u32 s_tmp[32];
+    __shared__ u32 s_nh[TPB];
     __shared__ u64 s_head;
     __shared__ u32 s_desc, s_set;
     LoopState* ls = ws.ls;
     const u64 s = ls->scan_pos, e = ls->scan_end, carry = ls->carry_head;
     const u32 cdesc = ls->carry_desc;
-    const u64 nt = e > s ? (e - s + kScanTile - 1) / kScanTile : 0;
-    if (threadIdx.x == 0) s_set = 0;
+    const u32 nt = (u32)(e > s ? (e - s + kScanTile - 1) / kScanTile : 0);
+    const int tid = threadIdx.x;
+    if (tid == 0) s_set = 0;
+    // this thread's tiles [t0, t1): descents before a first head, first tile with a head
+    const u32 per = (nt + TPB - 1) / TPB;
+    const u32 t0 = (u32)tid * per < nt ? (u32)tid * per : nt, t1 = t0 + per < nt ? t0 + per : nt;
+    u32 c = 0, fh = nt;
+    for (u32 t = t0; t < t1; ++t) {
+        const ScanTile tl = ws.scan_tiles[t];
+        c += tl.desc_first ? 1u : 0u;
+        if (fh == nt && tl.first_head != kNoHead) fh = t;
+    }
+    u32 tot;
+    u32 pd = block_exclusive_scan<u32>(c, s_tmp, &tot);
+    // smallest first-head tile of the threads after this one (suffix minimum)
+    s_nh[tid] = fh;
     __syncthreads();
-    for (u64 i = threadIdx.x; i < nt + 1; i += blockDim.x) {
+    for (int off = 1; off < TPB; off <<= 1) {
+        const u32 o = tid + off < TPB ? s_nh[tid + off] : nt;
+        __syncthreads();
+        if (o < s_nh[tid]) s_nh[tid] = o;
+        __syncthreads();
+    }
+    u32 nh = tid + 1 < TPB ? s_nh[tid + 1] : nt;
+    for (u32 t = t1; t > t0; --t) {
+        if (ws.scan_tiles[t - 1].first_head != kNoHead) nh = t - 1;
+        ws.scan_tiles[t - 1].next_head_tile = nh;
+    }
+    for (u32 t = t0; t < t1; ++t) {
+        ws.scan_tiles[t].desc_before = pd;
+        pd += ws.scan_tiles[t].desc_first ? 1u : 0u;
+    }
+    __syncthreads();                               // the tile fields are visible to the whole CTA
+    for (u32 i = tid; i < nt + 1; i += TPB) {
         u64 start;
         u32 desc;
         if (i == 0) {
@@ -418,16 +472,16 @@ __global__ void __launch_bounds__(1024) k_scan_link(Workspace<T> ws, u64 n, u32 
             start = tl.last_head;
             desc = tl.desc_last;
         }
-        u64 end = kNoHead;
-        for (u64 u = i; u < nt; ++u) {
-            const ScanTile tu = ws.scan_tiles[u];
-            desc |= tu.desc_first;
-            if (tu.first_head != kNoHead) {
-                end = tu.first_head;
-                break;
-            }
-        }
-        if (end == kNoHead) {
+        // tiles i .. u* (u* the next tile with a head) add their descents before a first head
+        const u32 us = i < nt ? ws.scan_tiles[i].next_head_tile : nt;
+        const u32 before_i = i < nt ? ws.scan_tiles[i].desc_before : tot;
+        u64 end;
+        if (us < nt) {
+            const ScanTile tu = ws.scan_tiles[us];
+            if (tu.desc_before + (tu.desc_first ? 1u : 0u) > before_i) desc = 1;
+            end = tu.first_head;
+        } else {
+            if (tot > before_i) desc = 1;
             if (e < n) {                       // carried into the next window
                 s_head = start;
                 s_desc = desc;
@@ -439,7 +493,7 @@ __global__ void __launch_bounds__(1024) k_scan_link(Workspace<T> ws, u64 n, u32 
         if (desc) strict_emit<T>(ws, Task{start, end - start}, rec_cap);
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
         ls->scan_pos = e;
         if (e >= n) {
             ls->carry_head = kNoHead;
