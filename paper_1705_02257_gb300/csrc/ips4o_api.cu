@@ -440,17 +440,21 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
     if (cudaPointerGetAttributes(&attr, h_ptr) == cudaSuccess && attr.type == cudaMemoryTypeHost)
         h_dev = attr.devicePointer;
     cudaGetLastError();   // a plain pageable pointer may leave a query error behind
-    bool by_kernel = false;
+    bool by_kernel = false, written = false;
     if (h_dev && key_type != IPS4O_REC100_K10 && (uintptr_t)h_dev % elem_align(key_type) == 0) {
         // pinned host memory and an element type sorted in place: the first
         // distribution level reads the host buffer itself and writes its
-        // blocks into the device copy (no separate copy pass)
+        // blocks into the device copy (no separate copy pass), and the base
+        // case writes each sorted bucket straight back into the host buffer;
+        // the ranges it does not write (equality buckets, single elements,
+        // subproblems of the segment scheduler) are copied back by a kernel
         by_kernel = true;
+        written = true;
         switch (key_type) {
-        case IPS4O_U64: rc = sort_from_u64(*st, st->d_host_copy, h_dev, n, s); break;
-        case IPS4O_F64: rc = sort_from_f64(*st, st->d_host_copy, h_dev, n, s); break;
-        case IPS4O_QUARTET_U64: rc = sort_from_quartet(*st, st->d_host_copy, h_dev, n, s); break;
-        default: rc = sort_from_pair(*st, st->d_host_copy, h_dev, n, s); break;
+        case IPS4O_U64: rc = sort_from_u64(*st, st->d_host_copy, h_dev, n, s, h_dev); break;
+        case IPS4O_F64: rc = sort_from_f64(*st, st->d_host_copy, h_dev, n, s, h_dev); break;
+        case IPS4O_QUARTET_U64: rc = sort_from_quartet(*st, st->d_host_copy, h_dev, n, s, h_dev); break;
+        default: rc = sort_from_pair(*st, st->d_host_copy, h_dev, n, s, h_dev); break;
         }
         publish_stats(*st);
         if (rc != IPS4O_OK) return rc;
@@ -466,7 +470,9 @@ ips4o_status ips4o_sort_host(void* h_ptr, size_t n, int key_type, void* stream) 
         rc = dispatch(*st, st->d_host_copy, n, key_type, s, nullptr);
         if (rc != IPS4O_OK) return rc;
     }
-    if (by_kernel && kernel_copy(h_dev, st->d_host_copy, bytes, s, st->sms, &e)) {
+    if (written) {
+        // the result is already in the host buffer
+    } else if (by_kernel && kernel_copy(h_dev, st->d_host_copy, bytes, s, st->sms, &e)) {
         if (e != cudaSuccess) { set_last_cuda_error(e, "copy kernel (D2H)"); return IPS4O_ERR_CUDA; }
     } else {
         e = cudaMemcpyAsync(h_ptr, st->d_host_copy, bytes, cudaMemcpyDeviceToHost, s);

@@ -186,13 +186,18 @@ __device__ void cta_bitonic(typename T::elem_t* s, u32 n) {
 // Sub-buckets of more than LIMIT elements (clustered or repeated keys) are
 // handled afterwards, one at a time by the whole CTA: left as they are when
 // all their keys are equal, else sorted in shared memory by a bitonic
-// network, so the cost stays bounded for any input.
+// network, so the cost stays bounded for any input.  With out, the sorted
+// bucket is written to out[0..m) instead of back to g.
 template <class T, class C>
-__device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
+__device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem, typename T::elem_t* out = nullptr) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     constexpr int TPB = C::TPB, EPT = C::EPT, SPT = C::SUBS_PER_THREAD;
-    if (m < 2) return;
+    if (m < 2) {
+        if (out && m == 1 && threadIdx.x == 0) out[0] = g[0];
+        return;
+    }
+    E* go = out ? out : g;
     E* data = (E*)(smem + C::off_data);
     u32* off = (u32*)(smem + C::off_off);          // sub-bucket sizes, then (scanned) starts
     K* tmp = (K*)(smem + C::off_tmp);
@@ -232,7 +237,14 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     }
     const bool all_equal = lo == hi;
     __syncthreads();                               // every thread has read tmp before it is reused
-    if (all_equal) return;                         // all keys equal: already sorted (uniform exit)
+    if (all_equal) {                               // all keys equal: already sorted (uniform exit)
+        if (out) {
+#pragma unroll
+            for (int q = 0; q < EPT; ++q)
+                if (tid + q * TPB < m) out[tid + q * TPB] = e[q];
+        }
+        return;
+    }
     u32 KB = pow2_ceil_u32((m + C::N0 - 1) / C::N0);
     KB = KB < 2 ? 2 : (KB > (u32)C::MAXSUB ? (u32)C::MAXSUB : KB);
     // sub-bucket = (key - lo) >> shift, with shift chosen so that the whole
@@ -294,8 +306,8 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
     __syncthreads();
     // final position = sub-bucket start + rank of the key within it
     // (elements of large sub-buckets are placed below)
-    // (not unrolled: the loop body holds the rank loop, and the unrolled copies
-    // cost more in instruction fetch than they save)
+    // (not unrolled: the loop body holds the rank loop, and the unrolled
+    // copies cost more in instruction fetch than they save)
 #pragma unroll 1
     for (int q = 0; q < EPT; ++q) {
         const u32 i = tid + q * TPB;
@@ -310,7 +322,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
                 const K kj = T::key(data[jj]);
                 r += (kj < k || (kj == k && jj < i)) ? 1u : 0u;
             }
-            g[o + r] = x;
+            go[o + r] = x;
         }
     }
     const u32 nbig = big_list[0];
@@ -322,7 +334,7 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
         int differs = 0;
         for (u32 i = tid; i < len; i += TPB) differs |= T::key(data[o + i]) != k0;
         if (__syncthreads_or(differs)) cta_bitonic<T, TPB>(data + o, len);
-        for (u32 i = tid; i < len; i += TPB) g[o + i] = data[o + i];
+        for (u32 i = tid; i < len; i += TPB) go[o + i] = data[o + i];
         __syncthreads();
     }
     __syncthreads();
@@ -330,16 +342,18 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem) {
 
 // Base-case tasks (buckets or whole small inputs): a persistent grid takes
 // tasks i = blockIdx.x, blockIdx.x + gridDim.x, ... of the list; the count is
-// read from device memory, so the launch does not depend on the host.
+// read from device memory, so the launch does not depend on the host.  With
+// out, each sorted bucket goes to the same range of out instead of arr.
 template <class T, class C>
 __global__ void __launch_bounds__(C::TPB, (C::TPB <= 256 ? 4 : (C::TPB <= 512 ? 2 : 1)))
-    k_base(typename T::elem_t* arr, const Task* tasks, const u32* count, ChunkCounters* ctr) {
+    k_base(typename T::elem_t* arr, const Task* tasks, const u32* count, ChunkCounters* ctr,
+           typename T::elem_t* out = nullptr) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const u32 n = *count;
     for (u32 i = blockIdx.x; i < n; i += gridDim.x) {
         const Task t = tasks[i];
         if (!IPS4O_GUARD(ctr, t.n <= (u64)C::CAP, t.n, C::CAP)) continue;
-        cta_sort<T, C>(arr + t.begin, (u32)t.n, smem_raw);
+        cta_sort<T, C>(arr + t.begin, (u32)t.n, smem_raw, out ? out + t.begin : nullptr);
     }
     if (threadIdx.x == 0 && blockIdx.x < n) {
         const u32 mine = (n - blockIdx.x + gridDim.x - 1) / gridDim.x;

@@ -238,7 +238,7 @@ struct ChunkCounters {
     u32 base_small;     // base-case tasks of the small size class
     u32 base_large;     // base-case tasks of the large size class
     u32 base_tiny;      // base-case tasks of the tiny size class
-    u32 pad2;
+    u32 copy_count;     // entries of the copy list (a sort whose result goes to another buffer)
     u64 blocks_moved;
     u64 blocks_skipped;
     u64 fix_blocks;
@@ -274,6 +274,7 @@ struct LoopState {
 };
 
 constexpr u64 kNoHead = ~0ull;
+constexpr u64 kCopyChunk = 1u << 16;   // elements per entry of the result copy list
 
 // Summary of one tile of the strict recursion's bucket-head scan.
 struct ScanTile {
@@ -317,10 +318,12 @@ struct Workspace {
     ChunkCounters* ctr;       // [1]
     Task* next_tasks2;        // [next_cap]      the second level queue of the device-planned recursion
     LoopState* ls;            // [1] device-planned recursion; null when the host plans the levels
+    Task* copy_tasks;         // [copy_cap] ranges final in arr that the result copy moves to out
+    elem_t* out;              // where the base case writes its sorted buckets (null: in place)
     key_t* scan_max;          // [scan_cap] strict recursion: largest key per scan tile, then the prefix before it
     ScanTile* scan_tiles;     // [scan_cap] strict recursion: heads and descents per scan tile
     u32 max_sub, max_stripes;
-    u64 pool_cap, next_cap, init_cap, stack_cap, scan_cap;
+    u64 pool_cap, next_cap, init_cap, stack_cap, scan_cap, copy_cap;
 };
 
 // ------------------------------------------------------------ primitives

@@ -44,7 +44,9 @@ struct Caps {
     u32 stack_slots = 0;   // segment scheduler: CTA stacks
     bool rounds = false;   // device-planned levels: a second task queue and the loop state
     u64 scan_cap = 0;      // strict recursion: tiles of one scan window
+    u64 copy_cap = 0;      // result written to another buffer: ranges the final copy moves
 };
+
 
 constexpr u64 kSegStackCap = 2048;     // per CTA; a distribution step pushes at most 256 buckets
 
@@ -98,7 +100,7 @@ Caps<T> caps_for(u64 n, int sms, int stripes_per_sm, u64 cap) {
 // subproblem a level can have (n / (threshold + 1)), and the segment
 // scheduler's per-CTA areas for subproblems left after the last round.
 template <class T>
-Caps<T> caps_for_rounds(u64 n, int sms, u64 cap) {
+Caps<T> caps_for_rounds(u64 n, int sms, u64 cap, bool copy_out = false) {
     const u64 B = T::kBlock, per = (u64)kMaxBuckets * (B - 1);
     Caps<T> c;
     const u64 stripes = kRoundStripesPerSm * (u64)std::max(1, sms);
@@ -114,6 +116,11 @@ Caps<T> caps_for_rounds(u64 n, int sms, u64 cap) {
     c.stack_slots = (u32)std::max<u64>(1, std::min<u64>({(u64)std::max(1, sms), (u64)c.max_sub,
                                                             (u64)c.max_stripes, c.pool_cap / per}));
     c.rounds = true;
+    // a result written to another buffer: the buckets the base case does not
+    // write (equality buckets, single elements: at most one chunk's buckets
+    // per round) and the segment scheduler's subproblems, in chunks of at
+    // most kCopyChunk elements
+    if (copy_out) c.copy_cap = (u64)c.max_sub * kMaxBuckets + c.init_cap + n / kCopyChunk + 64;
     return c;
 }
 
@@ -191,6 +198,8 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.next_tasks2 = c.rounds ? (Task*)take(c.next_cap * sizeof(Task)) : nullptr;
     w.ls = c.rounds ? (LoopState*)take(sizeof(LoopState)) : nullptr;
+    w.copy_tasks = c.copy_cap ? (Task*)take(c.copy_cap * sizeof(Task)) : nullptr;
+    w.out = nullptr;
     w.scan_max = c.scan_cap ? (K*)take(c.scan_cap * sizeof(K)) : nullptr;
     w.scan_tiles = c.scan_cap ? (ScanTile*)take(c.scan_cap * sizeof(ScanTile)) : nullptr;
     if (!base) {
@@ -204,6 +213,7 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.init_cap = c.init_cap;
     w.stack_cap = c.stack_cap;
     w.scan_cap = c.scan_cap;
+    w.copy_cap = c.copy_cap;
     if (ws) *ws = w;
     return align_up(off, 256);
 }
@@ -669,7 +679,17 @@ struct Driver {
         IPS4O_LAUNCH(5, (k_cleanup<T><<<8 * sms, CleanupCfg<T>::TPB, CleanupCfg<T>::smem_bytes, stream>>>(
                             d, ws, 0, 1, spin_limit(), 0u, rec_cap)));
         if (mark) IPS4O_LAUNCH(5, (k_mark<T, 512><<<4 * sms, 512, 0, stream>>>(d, ws, rec_cap)));
-        return launch_base_lists(d);
+        ips4o_status rc = launch_base_lists(d);
+        if (rc != IPS4O_OK) return rc;
+        return launch_copies(d);
+    }
+
+    // A result written to ws.out: the ranges of the copy list.
+    ips4o_status launch_copies(E* d) {
+        if (!ws.out) return IPS4O_OK;
+        IPS4O_LAUNCH(6, (k_copy_tasks<T><<<4 * st.sms, 256, 0, stream>>>(d, ws.out, ws.copy_tasks, &ws.ctr->copy_count,
+                                                                          ws.copy_cap)));
+        return IPS4O_OK;
     }
 
     // A sort that is one base case, with the loop state of the device-planned
@@ -678,13 +698,13 @@ struct Driver {
         IPS4O_LAUNCH(7, (k_plan_base<T><<<1, 32, 0, stream>>>(ws, n)));
         if (n <= (u64)T::kBaseTiny) {
             IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<1, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
-                                d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+                                d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr, ws.out)));
         } else if (n <= (u64)T::kBaseSmall) {
             IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<1, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
-                                d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+                                d, ws.base_small, &ws.ctr->base_small, ws.ctr, ws.out)));
         } else {
             IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<1, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
-                                d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+                                d, ws.base_large, &ws.ctr->base_large, ws.ctr, ws.out)));
         }
         IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
         return IPS4O_OK;
@@ -694,11 +714,11 @@ struct Driver {
     ips4o_status launch_base_lists(E* d) {
         const u32 sms = (u32)st.sms;
         IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
-                            d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr)));
+                            d, ws.base_tiny, &ws.ctr->base_tiny, ws.ctr, ws.out)));
         IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<2 * sms, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
-                            d, ws.base_small, &ws.ctr->base_small, ws.ctr)));
+                            d, ws.base_small, &ws.ctr->base_small, ws.ctr, ws.out)));
         IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
-                            d, ws.base_large, &ws.ctr->base_large, ws.ctr)));
+                            d, ws.base_large, &ws.ctr->base_large, ws.ctr, ws.out)));
         return IPS4O_OK;
     }
 
@@ -792,14 +812,15 @@ struct Driver {
     // the workspace must have been reserved (ips4o_reserve_workspace), since
     // nothing may be allocated; otherwise it grows as needed.  Statistics and
     // device-side errors are read back later (finalize_pending).
-    ips4o_status enqueue_sort(E* d, u64 n, const E* from = nullptr) {
+    ips4o_status enqueue_sort(E* d, u64 n, const E* from = nullptr, E* out = nullptr) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         IPS4O_CUDA(cudaStreamIsCapturing(stream, &cap));
         const bool capturing = cap != cudaStreamCaptureStatusNone;
         const u64 rc_cap = recursion_cap<T>(prm);
-        const Caps<T> c = caps_for_rounds<T>(n, st.sms, rc_cap);
+        const Caps<T> c = caps_for_rounds<T>(n, st.sms, rc_cap, out != nullptr);
         ips4o_status rc = setup(n, 0, &c, capturing ? kEnqueue : kGrow);
         if (rc != IPS4O_OK) return rc;
+        ws.out = out;                              // the base case and the copies write the result there
         st.stats.n = n;
         st.d_status = &ws.ls->status;
         if (!from) from = d;
@@ -828,6 +849,7 @@ struct Driver {
             const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
             IPS4O_LAUNCH(4, (k_segments<T><<<fallback_grid<T>(c), SegCfg<T>::TPB, SegCfg<T>::smem_bytes,
                                              stream>>>(d, ws, sq, prm.seed, k_max, spin_limit())));
+            if ((rc = launch_copies(d)) != IPS4O_OK) return rc;
             IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
         }
         st.pending = true;
@@ -1031,9 +1053,9 @@ ips4o_status sort_t(DeviceState& st, void* d, size_t n, cudaStream_t s, Partitio
 // d[0, n) = the sorted elements of src[0, n) (src device-accessible, e.g. the
 // device address of pinned host memory; src is only read), enqueued.
 template <class T>
-ips4o_status sort_from_t(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s) {
+ips4o_status sort_from_t(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out) {
     Driver<T> drv(st, s);
-    return drv.enqueue_sort((typename T::elem_t*)d, (u64)n, (const typename T::elem_t*)src);
+    return drv.enqueue_sort((typename T::elem_t*)d, (u64)n, (const typename T::elem_t*)src, (typename T::elem_t*)out);
 }
 
 // The strictly in-place sort of d[0, n) (Section 4.6); returns when the

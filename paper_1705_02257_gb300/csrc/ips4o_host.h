@@ -72,9 +72,9 @@ ips4o_status sort_u64(DeviceState& st, void* d, size_t n, cudaStream_t s, Partit
 ips4o_status sort_f64(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
 ips4o_status sort_pair(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
 // d = the sorted elements of src (device-accessible, only read; n elements)
-ips4o_status sort_from_u64(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s);
-ips4o_status sort_from_f64(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s);
-ips4o_status sort_from_pair(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s);
+ips4o_status sort_from_u64(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out);
+ips4o_status sort_from_f64(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out);
+ips4o_status sort_from_pair(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out);
 struct Task;
 ips4o_status sort_segments_u64(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
 ips4o_status enqueue_segments_u64(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count, cudaStream_t s);
@@ -101,7 +101,7 @@ ips4o_status reserve_u64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_f64(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status reserve_pair(DeviceState& st, size_t n, size_t num_segments);
 ips4o_status sort_quartet(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part);
-ips4o_status sort_from_quartet(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s);
+ips4o_status sort_from_quartet(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out);
 ips4o_status sort_segments_quartet(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s);
 ips4o_status enqueue_segments_quartet(DeviceState& st, void* d, const uint64_t* d_off, uint64_t count,
                                       cudaStream_t s);

@@ -1399,6 +1399,36 @@ __device__ __forceinline__ void emit_bucket(const Workspace<T>& ws, Task task, u
     }
 }
 
+// A final range [begin, begin + size) of the array that the base case will
+// not write to ws.out (an equality bucket, a single element, a subproblem
+// the segment scheduler sorts in place): queued for the result copy in
+// pieces of at most kCopyChunk elements.  One thread.
+template <class T>
+__device__ __forceinline__ void emit_copy(const Workspace<T>& ws, u64 begin, u64 size) {
+    const u64 nch = (size + kCopyChunk - 1) / kCopyChunk;
+    const u32 first = atomicAdd(&ws.ctr->copy_count, (u32)nch);
+    for (u64 c = 0; c < nch; ++c) {
+        const u64 b = begin + c * kCopyChunk, e = b + kCopyChunk < begin + size ? b + kCopyChunk : begin + size;
+        if ((u64)first + c < ws.copy_cap) ws.copy_tasks[first + c] = Task{b, e - b};
+        else set_status(ws.ctr, kStatusCapacity);
+    }
+}
+
+// The result copy: src[t.begin, t.begin + t.n) to dst for every entry t of
+// the copy list, one warp per entry.
+template <class T>
+__global__ void __launch_bounds__(256) k_copy_tasks(const typename T::elem_t* src, typename T::elem_t* dst,
+                                                    const Task* tasks, const u32* count, u64 cap) {
+    const u32 n = (u64)*count < cap ? *count : (u32)cap;
+    const int lane = threadIdx.x & 31;
+    const u32 warps = gridDim.x * (blockDim.x / 32);
+    for (u32 i = (blockIdx.x * blockDim.x + threadIdx.x) / 32; i < n; i += warps) {
+        const Task t = tasks[i];
+#pragma unroll 4
+        for (u64 k = lane; k < t.n; k += 32) dst[t.begin + k] = src[t.begin + k];
+    }
+}
+
 // One warp per (subproblem, bucket), taken in ticket order; WPC warps per CTA
 // (subproblems with few stripes: the lower levels).
 template <class T>
@@ -1496,7 +1526,11 @@ __device__ __forceinline__ void cleanup_bucket_warp(typename T::elem_t* arr, con
     if (partition_only) return;
     const u64 size = Eb - Bb;
     const bool is_eq = sub.eq && (b & 1);
-    if (is_eq || size < 2 || lane != 0) return;
+    if (lane != 0) return;
+    if (is_eq || size < 2) {                        // final: all keys equal, or one element
+        if (ws.out && size > 0) emit_copy<T>(ws, sub.begin + Bb, size);
+        return;
+    }
     emit_bucket<T>(ws, Task{sub.begin + Bb, size}, rec_cap);
 }
 
@@ -1658,7 +1692,10 @@ __device__ void cleanup_bucket_cta(typename T::elem_t* arr, const Workspace<T>& 
     if (partition_only) return;
     const u64 size = Eb - Bb;
     const bool is_eq = sub.eq && (b & 1);
-    if (is_eq || size < 2) return;
+    if (is_eq || size < 2) {                        // final: all keys equal, or one element
+        if (ws.out && size > 0 && threadIdx.x == 0) emit_copy<T>(ws, sub.begin + Bb, size);
+        return;
+    }
     if (threadIdx.x == 0) emit_bucket<T>(ws, Task{sub.begin + Bb, size}, rec_cap);
 }
 

@@ -8,8 +8,8 @@ namespace ips4o {
 ips4o_status sort_quartet(DeviceState& st, void* d, size_t n, cudaStream_t s, PartitionOut* part) {
     return sort_t<TQuartet>(st, d, n, s, part);
 }
-ips4o_status sort_from_quartet(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s) {
-    return sort_from_t<TQuartet>(st, d, src, n, s);
+ips4o_status sort_from_quartet(DeviceState& st, void* d, const void* src, size_t n, cudaStream_t s, void* out) {
+    return sort_from_t<TQuartet>(st, d, src, n, s, out);
 }
 ips4o_status sort_segments_quartet(DeviceState& st, void* d, const std::vector<Task>& segs, cudaStream_t s) {
     return sort_segments_t<TQuartet>(st, d, segs, s);

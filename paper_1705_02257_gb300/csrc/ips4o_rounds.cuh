@@ -342,6 +342,8 @@ __global__ void __launch_bounds__(1024) k_rounds_done(Workspace<T> ws) {
     for (u32 i = threadIdx.x; i < rem + nxt; i += blockDim.x) {
         const Task t = i < rem ? ls->cur_q[ls->cur_pos + i] : ls->next_q[i - rem];
         if (i < cap) ws.init_tasks[i] = t;
+        // a result written elsewhere: the scheduler sorts these in place, the copy moves them
+        if (ws.out) emit_copy<T>(ws, t.begin, t.n);
     }
     if (threadIdx.x == 0) {
         const u32 total = (u64)(rem + nxt) <= cap ? rem + nxt : (u32)cap;

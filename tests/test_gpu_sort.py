@@ -215,14 +215,21 @@ def test_sort_host_roundtrip(ips4o):
 
 @pytest.mark.parametrize("kt,dist,n", [
     ("u64", "uniform", 3_000_017), ("u64", "exponential", 2_000_003), ("u64", "ones", 300_001),
-    ("u64", "uniform", 1000), ("u64", "two_dup", 16_384), ("f64", "uniform", 1_000_003),
-    ("pair", "root_dup", 1_500_001), ("pair", "uniform", 777), ("rec100", "uniform", 100_003),
+    ("u64", "ones", 3_000_001), ("u64", "two_dup", 3_000_017), ("u64", "eight_dup", 2_000_003),
+    ("u64", "sorted", 2_000_003), ("u64", "exponential", 6_000_011), ("u64", "root_dup", 1_000_003),
+    ("u64", "uniform", 1), ("u64", "uniform", 2), ("u64", "uniform", 1000), ("u64", "ones", 1000),
+    ("u64", "two_dup", 16_384), ("u64", "two_dup", 16_385), ("f64", "uniform", 1_000_003),
+    ("pair", "root_dup", 1_500_001), ("pair", "ones", 700_001), ("pair", "uniform", 777),
+    ("quartet", "two_dup", 1_000_003), ("rec100", "uniform", 100_003),
 ])
 def test_sort_host_pinned(ips4o, kt, dist, n):
     """Pinned host buffers: the first distribution level reads the host
-    buffer through its device address (no separate copy pass); inputs no
-    larger than the base case are copied first.  The host buffer must end up
-    sorted and the input must not be needed afterwards."""
+    buffer through its device address (no separate copy pass), and the base
+    case writes each sorted bucket straight back into it; equality buckets,
+    single elements and subproblems of the segment scheduler are copied back
+    by a kernel.  Inputs no larger than the base case are copied first.  The
+    host buffer must end up sorted and the input must not be needed
+    afterwards."""
     a = inputs.make(kt, n, dist)
     h = torch.from_numpy(np.ascontiguousarray(a).view(np.uint8).reshape(-1).copy()).pin_memory()
     rc = ips4o.ips4o_sort_host(h.data_ptr(), n, ips4o.KEY_TYPES[kt], 0)
@@ -232,10 +239,29 @@ def test_sort_host_pinned(ips4o, kt, dist, n):
     if kt == "pair":
         assert np.array_equal(got["key"], exp["key"])
         assert np.array_equal(np.sort(got, order=["key", "payload"]), np.sort(a, order=["key", "payload"]))
+    elif kt == "quartet":
+        for f in ("k0", "k1", "k2"):
+            assert np.array_equal(got[f], exp[f]), f
+        assert oracle.multiset_hash(got, "quartet") == oracle.multiset_hash(a, "quartet")
     elif kt == "rec100":
         assert np.array_equal(got, exp)
     else:
         assert np.array_equal(got.view(np.uint64), exp.view(np.uint64))
+
+
+@pytest.mark.parametrize("dist", ["uniform", "two_dup", "exponential", "ones"])
+def test_sort_host_pinned_deep(ips4o, dist):
+    # a small base case and 4 buckets per step: many rounds, subproblems left
+    # to the segment scheduler, and many equality buckets copied back
+    a = inputs.u64(400_009, dist)
+    ips4o.set_params(base_case_max=64, k_max=4)
+    try:
+        h = torch.from_numpy(a.view(np.uint8).copy()).pin_memory()
+        rc = ips4o.ips4o_sort_host(h.data_ptr(), len(a), ips4o.U64, 0)
+    finally:
+        ips4o.reset_params()
+    assert rc == 0, ips4o.ips4o_status_string(rc)
+    assert np.array_equal(h.numpy().view(np.uint64), oracle.sort(a, "u64"))
 
 
 @pytest.mark.parametrize("dist", ["uniform", "two_dup", "exponential", "ones"])
