@@ -1063,8 +1063,8 @@ struct PermuteCfg {
     typedef typename T::key_t K;
     static constexpr int TPB = 128;
     static constexpr int NW = TPB / 32;
-    static constexpr int V = 8;                  // movers per warp (lanes 0..V-1)
-    static constexpr int MIN_CTAS = 6;           // register bound; shared memory admits 5 per SM (160 movers)
+    static constexpr int V = 16;                 // movers per warp (lanes 0..V-1)
+    static constexpr int MIN_CTAS = 3;           // shared memory admits 3 per SM (192 movers)
     // one block (512 bytes; 500 for 100-byte records) is copied by the warp
     // in chunks of CHB bytes, at most NCH per lane
     static constexpr int BB = T::kBlock * (int)sizeof(E);
