@@ -318,6 +318,7 @@ struct Workspace {
     ChunkCounters* ctr;       // [1]
     Task* next_tasks2;        // [next_cap]      the second level queue of the device-planned recursion
     LoopState* ls;            // [1] device-planned recursion; null when the host plans the levels
+    u32* stripe_order;        // [max_stripes] device-planned rounds: the order the classification takes stripes
     Task* copy_tasks;         // [copy_cap] ranges final in arr that the result copy moves to out
     elem_t* out;              // where the base case writes its sorted buckets (null: in place)
     key_t* scan_max;          // [scan_cap] strict recursion: largest key per scan tile, then the prefix before it

@@ -198,6 +198,7 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.ctr = (ChunkCounters*)take(sizeof(ChunkCounters));
     w.next_tasks2 = c.rounds ? (Task*)take(c.next_cap * sizeof(Task)) : nullptr;
     w.ls = c.rounds ? (LoopState*)take(sizeof(LoopState)) : nullptr;
+    w.stripe_order = c.rounds ? (u32*)take(R * sizeof(u32)) : nullptr;
     w.copy_tasks = c.copy_cap ? (Task*)take(c.copy_cap * sizeof(Task)) : nullptr;
     w.out = nullptr;
     w.scan_max = c.scan_cap ? (K*)take(c.scan_cap * sizeof(K)) : nullptr;
@@ -501,9 +502,25 @@ struct Driver {
         double best_score = -1e30;
         // a level split into several chunks anyway keeps the default
         const int w1 = count <= caps.max_sub ? w0 + 6 : w0;
+        u64 nmax = 0;
+        for (size_t i = 0; i < count; ++i) nmax = std::max<u64>(nmax, tasks[i].n);
         for (int wv = w0; wv <= w1; ++wv) {
-            u64 len = std::max<u64>((level_total + wv * sms - 1) / (wv * sms), kMinStripe);
+            const u64 K = (u64)wv * sms;
+            u64 len = std::max<u64>((level_total + K - 1) / K, kMinStripe);
             len = (len + B - 1) / B * B;
+            if (K >= count && nmax > len) {
+                // unequal subproblems: the smallest length (in blocks) whose
+                // stripes number at most K (see k_plan)
+                u64 lo = len / B, hi = (nmax + B - 1) / B;
+                while (lo < hi) {
+                    const u64 mid = (lo + hi) / 2;
+                    u64 c = 0;
+                    for (size_t i = 0; i < count; ++i) c += (tasks[i].n + mid * B - 1) / (mid * B);
+                    if (c <= K) hi = mid;
+                    else lo = mid + 1;
+                }
+                len = hi * B;
+            }
             u64 total = 0, pool = 0;
             for (size_t i = 0; i < count; ++i) {
                 const u64 ns = std::min<u64>(std::max<u64>(1, (tasks[i].n + len - 1) / len), kMaxStripesPerSub);
@@ -517,6 +534,7 @@ struct Driver {
             const double score = (double)total / (double)(waves * sms) - 0.02 * (wv - w0);
             if (score > best_score + 1e-9) { best_score = score; best_len = len; }
             if (len == kMinStripe) break;                 // shorter stripes are not allowed
+            if (total == waves * sms) break;              // full waves: later candidates cannot score higher
         }
         return best_len;
     }

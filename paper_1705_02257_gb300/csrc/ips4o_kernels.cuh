@@ -846,7 +846,7 @@ __global__ void __launch_bounds__(ClassifyRegCfg<T>::TPB, 1)
         const u32 s = s_stripe;
         __syncthreads();
         if (s >= nstripes) break;
-        classify_stripe_reg<T>(arr, src, ws, s, smem_raw);
+        classify_stripe_reg<T>(arr, src, ws, ws.stripe_order ? ws.stripe_order[s] : s, smem_raw);
     }
 }
 

@@ -83,6 +83,8 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
     LoopState* ls = ws.ls;
     __shared__ u64 s_n[TPB];
     __shared__ u64 s_beg[TPB];
+    __shared__ u64 s_key[TPB];
+    __shared__ u32 s_ns[TPB], s_sb[TPB];
     __shared__ u64 s_tmp64[32];
     __shared__ u32 s_tmp32[32];
     __shared__ u32 s_work, s_newlevel, s_m, s_ns0;
@@ -130,16 +132,47 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
         // subproblem roundings: try w0, w0 + 1, ... stripes per SM and keep
         // the count whose last wave is fullest, with a small charge for
         // extra stripes (more partial buffers to clean up).
-        u64 part = 0;
-        for (u32 i = tid; i < cnt; i += TPB) part += q[i].n;
+        u64 part = 0, pmax = 0;
+        for (u32 i = tid; i < cnt; i += TPB) {
+            part += q[i].n;
+            pmax = q[i].n > pmax ? q[i].n : pmax;
+        }
         const u64 total = block_sum<u64>(part, s_tmp64);
+        for (int o = 16; o > 0; o >>= 1) {
+            const u64 v = __shfl_xor_sync(0xffffffffu, pmax, o);
+            pmax = v > pmax ? v : pmax;
+        }
+        if ((tid & 31) == 0) s_n[tid >> 5] = pmax;
+        __syncthreads();
+        u64 nmax = 0;
+        for (int w = 0; w < TPB / 32; ++w) nmax = s_n[w] > nmax ? s_n[w] : nmax;
+        __syncthreads();
         const u32 w1 = cnt <= ws.max_sub ? pa.w0 + 6 : pa.w0;
         u64 best_len = 0;
         double best_score = -1e30;
         for (u32 wv = pa.w0; wv <= w1; ++wv) {
-            u64 len = (total + (u64)wv * pa.sms - 1) / ((u64)wv * pa.sms);
+            const u64 K = (u64)wv * pa.sms;
+            u64 len = (total + K - 1) / K;
             len = len < kMinStripe ? kMinStripe : len;
             len = (len + B - 1) / B * B;
+            if (K >= cnt && nmax > len) {
+                // With subproblems of unequal sizes the length total / K
+                // rounds each of them up to whole stripes and gives fewer,
+                // uneven waves (256 subproblems of about 2^20 keys, one
+                // stripe each, are 1.68 waves of 152 SMs).  The smallest
+                // length (in blocks) whose stripes number at most K splits
+                // only the largest subproblems and fills the waves.
+                u64 lo = len / B, hi = (nmax + B - 1) / B;   // count(hi * B) = cnt <= K
+                for (int it = 0; it < 24 && lo < hi; ++it) {
+                    const u64 mid = (lo + hi) / 2;
+                    u64 c = 0;
+                    for (u32 i = tid; i < cnt; i += TPB) c += (q[i].n + mid * B - 1) / (mid * B);
+                    c = block_sum<u64>(c, s_tmp64);
+                    if (c <= K) hi = mid;
+                    else lo = mid + 1;
+                }
+                len = hi * B;
+            }
             u64 ns_part = 0, pool_part = 0;
             for (u32 i = tid; i < cnt; i += TPB) {
                 u32 ns;
@@ -160,6 +193,7 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
                 best_len = len;
             }
             if (len == kMinStripe) break;               // shorter stripes are not allowed
+            if (tot_ns == waves * pa.sms) break;       // full waves: later candidates cannot score higher
         }
         if (tid == 0) {
             ls->stripe_len = best_len;
@@ -205,8 +239,8 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
     }
     __syncthreads();
     const u32 m = s_m;
-    // largest subproblems first: their stripes are handed out first, so the
-    // dynamic stripe scheduler ends the chunk with short ones
+    // largest subproblems first (the block permutation hands out its movers
+    // in this order too)
     u32 P = 1;
     while (P < m) P <<= 1;
     s_n[tid] = (u32)tid < m ? q[pos + tid].n : 0;
@@ -320,6 +354,40 @@ __global__ void __launch_bounds__(1024) k_plan(Workspace<T> ws, PlanArgs pa) {
         ls->subproblems += m;
         ls->elements_distributed += elems;
         ls->chunks += 1;
+    }
+    // the order in which the classification takes the chunk's stripes:
+    // longest first, so that the dynamic stripe scheduler approximates
+    // largest-first scheduling and ends the level with short stripes (the
+    // subproblems themselves stay largest first: the block permutation hands
+    // out its movers in their order)
+    if (ws.stripe_order) {
+        s_ns[tid] = (u32)tid < m ? ns_i : 0u;
+        s_sb[tid] = sbeg;
+        s_key[tid] = (u32)tid < m ? slen_i : 0;
+        s_beg[tid] = (u64)tid;
+        __syncthreads();
+        for (u32 k = 2; k <= P; k <<= 1) {
+            for (u32 jj = k >> 1; jj > 0; jj >>= 1) {
+                const u32 i = (u32)tid, ixj = i ^ jj;
+                if (i < P && ixj > i) {
+                    const bool desc = (i & k) == 0;
+                    const u64 a = s_key[i], b = s_key[ixj];
+                    if (desc ? a < b : a > b) {
+                        s_key[i] = b;
+                        s_key[ixj] = a;
+                        const u64 t = s_beg[i];
+                        s_beg[i] = s_beg[ixj];
+                        s_beg[ixj] = t;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        const u32 j = (u32)s_beg[tid];
+        const u32 nsj = (u32)tid < m ? s_ns[j] : 0u;
+        u32 tot;
+        const u32 o = block_exclusive_scan<u32>(nsj, s_tmp32, &tot);
+        for (u32 q2 = 0; q2 < nsj; ++q2) ws.stripe_order[o + q2] = s_sb[j] + q2;
     }
 }
 
