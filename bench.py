@@ -491,18 +491,31 @@ def run_batched(args):
         from paper_1705_02257_gb300 import autotune
         tuned = autotune.tune("u64", classes=range(14, 21), dist=args.dist,
                               scheduler=args.segment_scheduler or 1)
-    if args.segment_scheduler:
+    if args.segment_scheduler in (1, 2):
         ips4o.set_params(segment_scheduler=args.segment_scheduler)
     off_host = np.ascontiguousarray(off)
+    enqueue_only = args.segment_scheduler == 3
+    if enqueue_only:
+        # ips4o_sort_segmented_async: offsets on the device, workspace reserved
+        d_off = torch.from_numpy(off_host.view(np.int64).copy()).cuda()
+        rc = ips4o.ips4o_reserve_workspace(total, nseg, ips4o.U64, stream.cuda_stream)
+        if rc:
+            raise ips4o.Ips4oError(rc, "ips4o_reserve_workspace")
 
     def one_step():
         work.copy_(pristine)
         torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         s.record(stream)
-        rc = ips4o.ips4o_sort_segmented(work.data_ptr(), off_host.ctypes.data, nseg, ips4o.U64, stream.cuda_stream)
+        if enqueue_only:
+            rc = ips4o.ips4o_sort_segmented_async(work.data_ptr(), d_off.data_ptr(), nseg, ips4o.U64,
+                                                  stream.cuda_stream)
+        else:
+            rc = ips4o.ips4o_sort_segmented(work.data_ptr(), off_host.ctypes.data, nseg, ips4o.U64, stream.cuda_stream)
         e.record(stream)
         torch.cuda.synchronize()
+        if rc == 0 and enqueue_only:
+            rc = ips4o.ips4o_stream_status(stream.cuda_stream)
         if rc:
             raise ips4o.Ips4oError(rc, "ips4o_sort_segmented")
         return s.elapsed_time(e)
@@ -597,7 +610,7 @@ def run_batched(args):
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": f"batched segmented sort: {label}, log-uniform lengths [16, 2^20] (seed 4), "
                                f"{args.dist} keys per array, one ips4o_sort_segmented call "
-                               f"({['automatic', 'level by level', 'segment scheduler'][args.segment_scheduler]})",
+                               f"({['automatic', 'level by level', 'segment scheduler', 'enqueue-only ips4o_sort_segmented_async'][args.segment_scheduler]})",
                    "segments": nseg, "n": total, "key_type": "u64", "distribution": args.dist,
                    "l2": f"{total * 8 / 2**30:.1f} GiB per step, larger than L2",
                    "parallelism": f"replicas x{world}"},
@@ -758,8 +771,9 @@ def main():
                     help="100-byte records: 0 key + index indirection (default), 1 in-place blocks")
     ap.add_argument("--strict", action="store_true",
                     help="plain workload: time ips4o_sort_strict (Section 4.6, workspace independent of n)")
-    ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2],
-                    help="batched: 0 automatic, 1 level by level, 2 one CTA per array")
+    ap.add_argument("--segment-scheduler", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="batched: 0 automatic, 1 level by level, 2 one CTA per array, "
+                         "3 the enqueue-only ips4o_sort_segmented_async")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -249,19 +249,25 @@ ips4o_status ips4o_sort_segmented(void* d_base, const uint64_t* offsets, size_t 
  * d_offsets (num_segments + 1 element indices) must be in DEVICE memory, the
  * call only enqueues kernels on `stream` (it neither allocates, nor copies
  * to or from the host, nor synchronises), so it can be captured into a CUDA
- * graph and replayed.  The arrays are sorted by the segment scheduler: one
- * persistent launch in which each CTA sorts whole arrays (the distribution
- * steps and the base case of one array by one CTA), largest arrays first,
- * after three small kernels that build that queue on the device.
+ * graph and replayed.  The levels are planned on the device as for
+ * ips4o_sort: the segments no larger than the base case are sorted by the
+ * base case at once, the larger ones form the first level's queue, and each
+ * level distributes all its subproblems side by side (Section 4); what is
+ * left after the enqueued rounds is sorted by the segment scheduler (one CTA
+ * per array).  With params.segment_scheduler = 2 every segment goes to the
+ * segment scheduler instead.
  *   - The workspace of (current device, stream) must have been reserved
- *     with ips4o_reserve_workspace(n >= 1, num_segments, key_type, stream);
- *     otherwise IPS4O_ERR_TOO_LARGE is returned and nothing is enqueued.
+ *     with ips4o_reserve_workspace(n, num_segments, key_type, stream), n at
+ *     least the total number of elements of the segments (the level queues
+ *     are sized from it; a larger total makes ips4o_stream_status report
+ *     IPS4O_ERR_INTERNAL); without a reservation IPS4O_ERR_TOO_LARGE is
+ *     returned and nothing is enqueued.
  *   - Device-side errors (decreasing offsets, a bounded wait that gave up,
  *     a broken invariant) are recorded in the stream's status word:
  *     ips4o_stream_status(stream) waits for the stream and returns them.
- *   - ips4o_get_stats does not report these calls.  u64, f64 and pair only.
- * Segments of any length are sorted; each runs on one SM, so arrays much
- * longer than 2^22 elements are better served by ips4o_sort_segmented. */
+ *   - ips4o_get_stats (which waits for the stream) reports the call's
+ *     counters, with n = 0 (the total is known on the device only).
+ *     u64, f64, pair and quartet keys. */
 ips4o_status ips4o_sort_segmented_async(void* d_base, const uint64_t* d_offsets, size_t num_segments,
                                         int key_type, void* stream);
 

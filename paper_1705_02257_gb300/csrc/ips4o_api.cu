@@ -550,6 +550,7 @@ ips4o_status ips4o_release_workspace(void) {
         st->events.clear();
         st->d_ws = st->d_host_copy = st->d_aux = st->h_stage = nullptr;
         st->d_status = nullptr;
+        for (int k = 0; k < 5; ++k) st->reserved_n[k] = st->reserved_segments[k] = 0;
         st->ws_bytes = st->d_host_copy_bytes = st->aux_bytes = st->h_stage_bytes = 0;
     }
     return IPS4O_OK;

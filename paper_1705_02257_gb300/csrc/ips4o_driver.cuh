@@ -124,6 +124,21 @@ Caps<T> caps_for_rounds(u64 n, int sms, u64 cap, bool copy_out = false) {
     return c;
 }
 
+// Workspace of the enqueue-only segmented sort planned on the device: the
+// rounds' tables and queues, a list for every segment, and the leftover pool
+// of the level-by-level host driver (many segments above the base case each
+// take at least one stripe and its pool area, so a larger pool keeps the
+// first level in fewer chunks).
+template <class T>
+Caps<T> caps_for_segment_rounds(u64 n, int sms, u64 cap, u64 num_segments) {
+    Caps<T> c = caps_for_rounds<T>(n, sms, cap);
+    const Caps<T> h = caps_for<T>(n, sms, 1, cap);
+    c.init_cap = std::max<u64>(c.init_cap, num_segments);
+    c.pool_cap = std::max<u64>(c.pool_cap, h.pool_cap);
+    c.max_stripes = std::max<u32>(c.max_stripes, h.max_stripes);
+    return c;
+}
+
 // Elements of one window of the strict recursion's scan: about 1 GiB, a
 // whole number of scan tiles; params.strict_window overrides it.
 template <class T>
@@ -981,6 +996,63 @@ struct Driver {
     // work: no allocation, no host synchronisation (capturable in a CUDA
     // graph).  The workspace must have been reserved.  Errors land in the
     // status word that ips4o_stream_status reads.
+    // The enqueue-only segmented sort with the recursion planned on the
+    // device, as in enqueue_sort: the segments no larger than the base case
+    // are sorted by the base case at once, the larger ones are the first
+    // level's queue, and the rounds distribute them level by level (all
+    // segments of a level side by side, Section 4's subproblems).  The level
+    // queues are sized for the n the workspace was reserved for.  The host
+    // does not know the segments' sizes, so it enqueues the rounds of the
+    // reserved n plus one round per chunk the first level may need (each
+    // segment above the base case takes at least one stripe and its pool
+    // area); subproblems the rounds leave go to the segment scheduler.
+    ips4o_status enqueue_segments_rounds(E* d, const u64* d_off, u64 num_segments, u64 n_res) {
+        const u64 rc_cap = recursion_cap<T>(prm);
+        const Caps<T> c = caps_for_segment_rounds<T>(n_res, st.sms, rc_cap, num_segments);
+        ips4o_status rc = setup(n_res, 0, &c, kEnqueue);
+        if (rc != IPS4O_OK) return rc;
+        st.stats.n = 0;                            // the total is known on the device only
+        st.d_status = &ws.ls->status;
+        const u32 sms = (u32)st.sms;
+        IPS4O_LAUNCH(7, (k_seg_rounds_init<T><<<1, 32, 0, stream>>>(ws)));
+        const int g = (int)std::min<u64>((num_segments + 255) / 256, (u64)sms * 4);
+        IPS4O_LAUNCH(7, (k_seg_big_hist<T><<<g, 256, 0, stream>>>(d_off, num_segments, ws, (u32)rc_cap)));
+        IPS4O_LAUNCH(7, (k_seg_scan<<<1, 32, 0, stream>>>(ws.hist, &ws.ls->cur_count, &ws.ls->cur_pos)));
+        IPS4O_LAUNCH(7, (k_seg_split<T><<<g, 256, 0, stream>>>(d_off, num_segments, ws, (u32)rc_cap)));
+        // the base-case segments: one launch per size class over the whole list
+        IPS4O_LAUNCH(6, (k_base<T, BaseTiny<T>><<<4 * sms, BaseTiny<T>::TPB, BaseTiny<T>::smem_bytes, stream>>>(
+                            d, ws.init_tasks, ws.init_count, ws.ctr, nullptr, 0, (u64)T::kBaseTiny)));
+        IPS4O_LAUNCH(6, (k_base<T, BaseSmall<T>><<<2 * sms, BaseSmall<T>::TPB, BaseSmall<T>::smem_bytes, stream>>>(
+                            d, ws.init_tasks, ws.init_count, ws.ctr, nullptr, (u64)T::kBaseTiny, (u64)T::kBaseSmall)));
+        IPS4O_LAUNCH(6, (k_base<T, BaseLarge<T>><<<sms, BaseLarge<T>::TPB, BaseLarge<T>::smem_bytes, stream>>>(
+                            d, ws.init_tasks, ws.init_count, ws.ctr, nullptr, (u64)T::kBaseSmall, ~0ull)));
+        PlanArgs pa{};
+        pa.n = n_res;
+        pa.k_max = k_max;
+        pa.alpha = prm.alpha > 0 ? (u32)prm.alpha : (u32)kDefaultAlpha;
+        pa.base_cap = base_cap;
+        pa.sms = sms;
+        pa.w0 = (u32)std::max(1, prm.stripes_per_sm);
+        const u64 per = (u64)kMaxBuckets * (T::kBlock - 1);
+        const u64 first_level = std::min<u64>(num_segments, n_res / (rc_cap + 1) + 1);
+        const u64 per_chunk = std::max<u64>(1, std::min<u64>(c.max_sub, c.pool_cap / per));
+        const u32 R = rounds_for(n_res, rc_cap, base_cap, k_max, c.max_sub) + (u32)((first_level + per_chunk - 1) / per_chunk);
+        for (u32 r = 0; r < R; ++r) {
+            pa.newlevel = r == 0 ? 1u : 0u;         // the first round plans the first level
+            pa.level = 0;
+            if ((rc = launch_round(d, d, pa, false)) != IPS4O_OK) return rc;
+        }
+        IPS4O_LAUNCH(7, (k_rounds_done<T><<<1, 1024, 0, stream>>>(ws)));
+        const SegQueue sq{ws.init_tasks, ws.init_count, ws.init_count + 1, ws.stacks, (u32)ws.stack_cap};
+        IPS4O_LAUNCH(4, (k_segments<T><<<fallback_grid<T>(c), SegCfg<T>::TPB, SegCfg<T>::smem_bytes, stream>>>(
+                            d, ws, sq, prm.seed, k_max, spin_limit())));
+        IPS4O_LAUNCH(7, (k_fold<T><<<1, 32, 0, stream>>>(ws)));
+        st.pending = true;
+        st.pending_ls = ws.ls;
+        st.pending_stream = stream;
+        return IPS4O_OK;
+    }
+
     ips4o_status enqueue_scheduler(E* d, const u64* d_off, u64 num_segments) {
         const Caps<T> c = caps_for_scheduler<T>(st.sms, num_segments);
         ips4o_status rc = setup(0, 0, &c, kEnqueue);
@@ -1101,11 +1173,15 @@ ips4o_status reserve_t(DeviceState& st, u64 n, u64 num_segments) {
     const ips4o_params& prm = global_params();
     Caps<T> c = caps_for<T>(n, st.sms, prm.stripes_per_sm, recursion_cap<T>(prm));
     c.init_cap = num_segments;
+    const Caps<T> cs = caps_for_segment_rounds<T>(n, st.sms, recursion_cap<T>(prm), num_segments);
     const size_t need = std::max({carve<T>(c, nullptr, nullptr),
                                   carve<T>(caps_for_scheduler<T>(st.sms, num_segments), nullptr, nullptr),
-                                  carve<T>(caps_for_rounds<T>(n, st.sms, recursion_cap<T>(prm)), nullptr, nullptr)});
+                                  carve<T>(caps_for_rounds<T>(n, st.sms, recursion_cap<T>(prm)), nullptr, nullptr),
+                                  carve<T>(cs, nullptr, nullptr)});
     ips4o_status rc = ensure_device_buffer(&st.d_ws, &st.ws_bytes, need);
     if (rc != IPS4O_OK) return rc;
+    st.reserved_n[T::kId] = std::max<u64>(st.reserved_n[T::kId], n);
+    st.reserved_segments[T::kId] = std::max<u64>(st.reserved_segments[T::kId], num_segments);
     if (!st.attrs_ready[T::kId] && (rc = set_kernel_attributes<T>(st)) != IPS4O_OK) return rc;
     return ensure_host_pinned(&st.h_stage, &st.h_stage_bytes, host_stage_bytes<T>(c));
 }
@@ -1134,7 +1210,12 @@ ips4o_status upload_class_table_t(const ips4o_class_params* t) {
 template <class T>
 ips4o_status enqueue_segments_t(DeviceState& st, void* d, const u64* d_off, u64 num_segments, cudaStream_t s) {
     Driver<T> drv(st, s);
-    return drv.enqueue_scheduler((typename T::elem_t*)d, d_off, num_segments);
+    // the device-planned levels need the total the workspace was reserved
+    // for; the segment scheduler (segment_scheduler = 2) needs none
+    const u64 n_res = st.reserved_n[T::kId];
+    if (global_params().segment_scheduler == 2 || n_res == 0)
+        return drv.enqueue_scheduler((typename T::elem_t*)d, d_off, num_segments);
+    return drv.enqueue_segments_rounds((typename T::elem_t*)d, d_off, num_segments, n_res);
 }
 
 }  // namespace ips4o

@@ -25,6 +25,11 @@ struct DeviceState {
     unsigned* d_status = nullptr;   // status word of the last enqueue-only call on this stream
     bool attrs_ready[5] = {false, false, false, false, false};   // kernel attributes set, per element type
     int permute_grid[5] = {0, 0, 0, 0, 0};
+    // largest n and segment count the workspace was reserved for, per element
+    // type (ips4o_reserve_workspace): the enqueue-only segmented sort sizes
+    // its level queues from them
+    uint64_t reserved_n[5] = {0, 0, 0, 0, 0};
+    uint64_t reserved_segments[5] = {0, 0, 0, 0, 0};
     std::vector<cudaEvent_t> events;
     struct Timed { int phase; int ev; };
     std::vector<Timed> timed;       // profiled launches whose events have not been read yet

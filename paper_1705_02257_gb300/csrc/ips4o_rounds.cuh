@@ -432,6 +432,65 @@ __global__ void k_fold(Workspace<T> ws) {
     }
 }
 
+// The loop state of an enqueue-only segmented sort: no subproblem yet.
+template <class T>
+__global__ void k_seg_rounds_init(Workspace<T> ws) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        *ws.ls = LoopState{};
+        ws.ls->cur_q = ws.next_tasks;
+        ws.ls->next_q = ws.next_tasks2;
+        *ws.ctr = ChunkCounters{};
+        ws.init_count[0] = 0;
+    }
+    for (int g = threadIdx.x; g < 65; g += blockDim.x) ws.hist[g] = 0;
+}
+
+// Size groups (2^(g-1) <= n < 2^g) of the segments above the base case, so
+// that the first level's queue can hold them largest group first: chunks of
+// the level then take subproblems of similar size, as the host driver's
+// sorted levels do.
+template <class T>
+__global__ void k_seg_big_hist(const u64* off, u64 num, Workspace<T> ws, u32 rec_cap) {
+    __shared__ u32 h[65];
+    for (int i = threadIdx.x; i < 65; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < num; i += (u64)gridDim.x * blockDim.x) {
+        const u64 n = off[i + 1] >= off[i] ? off[i + 1] - off[i] : 0;
+        if (n > (u64)rec_cap) atomicAdd(&h[64 - __clzll((long long)n)], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 65; i += blockDim.x)
+        if (h[i]) atomicAdd(&ws.hist[i], h[i]);
+}
+
+// The segments [off[i], off[i + 1]) of an enqueue-only segmented sort: those
+// no larger than the base case go to init_tasks (sorted by the base case
+// straight away), the larger ones form the first level's queue, largest
+// size group first.  Offsets that decrease are an error of the call.
+template <class T>
+__global__ void k_seg_split(const u64* off, u64 num, Workspace<T> ws, u32 rec_cap) {
+    LoopState* ls = ws.ls;
+    for (u64 i = (u64)blockIdx.x * blockDim.x + threadIdx.x; i < num; i += (u64)gridDim.x * blockDim.x) {
+        const u64 b = off[i], e = off[i + 1];
+        if (e < b) {
+            atomicOr(&ls->status, kStatusInternal);
+            continue;
+        }
+        const u64 n = e - b;
+        if (n < 2) continue;
+        if (n <= (u64)rec_cap) {
+            const u32 idx = atomicAdd(&ws.init_count[0], 1u);
+            if (idx < ws.init_cap) ws.init_tasks[idx] = Task{b, n};
+            else atomicOr(&ls->status, kStatusCapacity);
+        } else {
+            // the place in its size group (k_seg_scan turned the group counts into starts)
+            const u32 idx = atomicAdd(&ws.hist[64 - __clzll((long long)n)], 1u);
+            if (idx < ws.next_cap) ls->cur_q[idx] = Task{b, n};
+            else atomicOr(&ls->status, kStatusCapacity);
+        }
+    }
+}
+
 // A sort that is one base case: the single task and the loop state.
 template <class T>
 __global__ void k_plan_base(Workspace<T> ws, u64 n) {

@@ -249,6 +249,49 @@ def test_segmented_async_and_stream_status(ips4o, kt, dist):
     check_segments(to_host(t, a), a, off, kt)
 
 
+@pytest.mark.parametrize("dist", ["uniform", "two_dup", "exponential"])
+def test_segmented_async_deep_recursion(ips4o, dist):
+    # a base case of 64 keys and 4 buckets per step: many levels planned on the
+    # device, and subproblems the enqueued rounds leave go to the segment
+    # scheduler; every segment equals the oracle's sort of it
+    lengths = inputs.log_uniform_lengths(300, 4, 17)
+    off = offsets_for(lengths)
+    a = inputs.make("u64", int(off[-1]), dist)
+    t = to_dev(a)
+    d_off = torch.from_numpy(off.view(np.int64).copy()).cuda()
+    stream = torch.cuda.Stream()
+    ips4o.set_params(base_case_max=64, k_max=4)
+    try:
+        assert ips4o.ips4o_reserve_workspace(int(off[-1]), len(lengths), ips4o.U64, stream.cuda_stream) == 0
+        torch.cuda.synchronize()
+        _async_sort(ips4o, t, d_off, len(lengths), "u64", stream)
+        assert ips4o.ips4o_stream_status(stream.cuda_stream) == 0
+    finally:
+        ips4o.reset_params()
+    check_segments(to_host(t, a), a, off, "u64")
+
+
+def test_segmented_async_more_keys_than_reserved(ips4o):
+    # the level queues are sized for the reserved total: segments holding
+    # more keys than that are reported as an internal error by
+    # ips4o_stream_status (no fault); a later call within the reservation works
+    lengths = np.full(64, 40_000, dtype=np.uint64)
+    off = offsets_for(lengths)
+    a = inputs.make("u64", int(off[-1]), "uniform")
+    t = to_dev(a)
+    d_off = torch.from_numpy(off.view(np.int64).copy()).cuda()
+    stream = torch.cuda.Stream()
+    assert ips4o.ips4o_reserve_workspace(100_000, len(lengths), ips4o.U64, stream.cuda_stream) == 0
+    torch.cuda.synchronize()
+    _async_sort(ips4o, t, d_off, len(lengths), "u64", stream)
+    assert ips4o.ips4o_stream_status(stream.cuda_stream) == 7
+    assert ips4o.ips4o_reserve_workspace(int(off[-1]), len(lengths), ips4o.U64, stream.cuda_stream) == 0
+    t = to_dev(a)
+    _async_sort(ips4o, t, d_off, len(lengths), "u64", stream)
+    assert ips4o.ips4o_stream_status(stream.cuda_stream) == 0
+    check_segments(to_host(t, a), a, off, "u64")
+
+
 def test_segmented_async_reports_decreasing_offsets(ips4o):
     t = torch.zeros(1000, dtype=torch.int64).cuda()
     off = torch.tensor([0, 500, 400, 1000], dtype=torch.int64).cuda()
