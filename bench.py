@@ -375,13 +375,20 @@ def run_gpu(args):
             if i >= args.warmup:
                 e2e_times.append(dt)
         e2e_total = sum(e2e_times)
+        # the last call's host result: non-decreasing, and for key-only types
+        # equal to the device-timed sort of the same input
+        t_chk = h_work.cuda()
+        e2e_sorted = bool(_sorted_keys(t_chk, kt))
+        e2e_same = bool(torch.equal(t_chk, work)) if kt in ("u64", "f64") else None
+        del t_chk
         if dist_on:
             t = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
             tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
             e2e_total = float(t.item())
         e2e = {"value": n * world * args.steps / e2e_total, "unit": METRIC,
                "h2d_bytes_per_step": n * elem, "d2h_bytes_per_step": n * elem,
-               "ms_per_step": 1e3 * e2e_total / args.steps, "host_memory": "pinned"}
+               "ms_per_step": 1e3 * e2e_total / args.steps, "host_memory": "pinned",
+               "output_sorted": e2e_sorted, "equals_device_result": e2e_same}
         # the transfer bound: the same bytes copied host -> device and back
         # by the copy engines (pinned buffers, CUDA events), no sort between
         e2e.update(_transfer_bound(h_in, pristine, stream, 4))
