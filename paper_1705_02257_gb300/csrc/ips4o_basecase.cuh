@@ -58,6 +58,70 @@ __device__ void sort_sample(K* keys, u32 P) {
     }
 }
 
+// The same bitonic network for a full sample of N keys (N a multiple of
+// TPB): each thread keeps N / TPB consecutive keys in registers, so the
+// stages whose partners lie in the same thread or the same warp need no
+// shared memory and no barrier; only the stages across warps go through
+// keys[] (about 10 of the 78 stages for 4096 keys and 512 threads).
+template <class K, int TPB, int N>
+__device__ void sort_sample_reg(K* keys) {
+    constexpr int R = N / TPB;
+    static_assert(R >= 1 && (R & (R - 1)) == 0 && N % TPB == 0, "whole power-of-two runs per thread");
+    const u32 tid = threadIdx.x;
+    K v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = keys[tid * R + r];
+    __syncthreads();
+    for (u32 k = 2; k <= (u32)N; k <<= 1) {
+        for (u32 j = k >> 1; j > 0; j >>= 1) {
+            if (j >= 32u * R) {
+                // partner in another warp: through shared memory
+#pragma unroll
+                for (int r = 0; r < R; ++r) keys[tid * R + r] = v[r];
+                __syncthreads();
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u32 i = tid * R + r;
+                    const K o = keys[i ^ j];
+                    const bool up = (i & k) == 0, low = (i & j) == 0;
+                    v[r] = (low == up) ? (o < v[r] ? o : v[r]) : (v[r] < o ? o : v[r]);
+                }
+                __syncthreads();
+            } else if (j >= (u32)R) {
+                // partner in another lane of this warp
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const u32 i = tid * R + r;
+                    const K o = shfl_xor_key(v[r], (int)(j / R));
+                    const bool up = (i & k) == 0, low = (i & j) == 0;
+                    v[r] = (low == up) ? (o < v[r] ? o : v[r]) : (v[r] < o ? o : v[r]);
+                }
+            } else {
+                // partner in this thread's registers (jr takes the value of j
+                // as a constant, so the registers are indexed statically)
+#pragma unroll
+                for (int jr = R / 2; jr >= 1; jr >>= 1) {
+                    if (j != (u32)jr) continue;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (r & jr) continue;
+                        const u32 i = tid * R + r;
+                        const bool up = (i & k) == 0;
+                        const K a = v[r], b = v[r | jr];
+                        if ((b < a) == up) {
+                            v[r] = b;
+                            v[r | jr] = a;
+                        }
+                    }
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) keys[tid * R + r] = v[r];
+    __syncthreads();
+}
+
 // From a sorted sample keys[0..alpha*kk-1), pick kk-1 equally spaced
 // splitters s_j = keys[j*alpha - 1] (Section 3), remove duplicates, and turn
 // on equality buckets when the sample repeated a splitter (Sections 4.4 and

@@ -59,7 +59,12 @@ __device__ void sample_sub(const typename T::elem_t* arr, const Workspace<T>& ws
         }
     }
     __syncthreads();
-    sort_sample<K, TPB>(keys, P);
+    if constexpr (T::kSampleMax % TPB == 0 && T::kSampleMax >= TPB) {
+        if (P == (u32)T::kSampleMax) sort_sample_reg<K, TPB, T::kSampleMax>(keys);   // the usual full sample
+        else sort_sample<K, TPB>(keys, P);
+    } else {
+        sort_sample<K, TPB>(keys, P);
+    }
     u32 logL;
     bool eq;
     select_splitters<K>(keys, kk, alpha, cand, scan_tmp, ws.tree + (u64)j * kMaxLeaves, ws.spl + (u64)j * kMaxLeaves,
