@@ -325,7 +325,10 @@ size_t ips4o_workspace_bytes(size_t n, int key_type);
  * ips4o_sort), so that such calls allocate nothing.  A service reserves its
  * workers' workspaces up front this way: allocation while other streams run
  * costs time, and freeing a smaller workspace synchronises the device.
- * Workspaces only grow; ips4o_release_workspace frees them. */
+ * Workspaces only grow; ips4o_release_workspace frees them.  The largest n
+ * reserved on (device, stream) for the key type is remembered: the
+ * enqueue-only ips4o_sort_segmented_async sizes its level queues from it, so
+ * n must be at least the total number of elements of its segments. */
 ips4o_status ips4o_reserve_workspace(size_t n, size_t num_segments, int key_type, void* stream);
 
 /* Free the workspaces and staging buffers held on the current device (all streams). */
