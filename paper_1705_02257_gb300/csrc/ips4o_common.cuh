@@ -299,6 +299,7 @@ struct Workspace {
     u64* wr;                  // [max_sub][256]   packed w_i, r_i, reader count (see kWShift)
     u32* flags;               // [max_sub][256]   cleanup hand-over flags
     u32* exhausted;           // [max_sub][8]     bitmap of buckets without unprocessed blocks
+    u32* movers;              // [max_sub]        CTAs working on the block permutation of each subproblem
     u32* region_full;         // [max_sub][256]   full blocks inside region [d_i, d_{i+1})
     u32* bucket_full;         // [max_sub][256]   full blocks of bucket i (all stripes)
     u32* counts;              // [max_stripes][256] elements per bucket per stripe
@@ -400,6 +401,11 @@ __device__ __forceinline__ void red_add_release(u32* p, u32 v) {
 __device__ __forceinline__ u32 ld_relaxed(const u32* p) {
     u32 v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ u64 ld_relaxed64(const u64* p) {
+    u64 v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
 }
 __device__ __forceinline__ void red_add_relaxed(u32* p, u32 v) {

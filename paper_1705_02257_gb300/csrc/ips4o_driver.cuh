@@ -194,6 +194,7 @@ size_t carve(const Caps<T>& c, char* base, Workspace<T>* ws) {
     w.wr = (u64*)take(S * kMaxBuckets * 8);
     w.flags = (u32*)take(S * kMaxBuckets * 4);
     w.exhausted = (u32*)take(S * 8 * 4);
+    w.movers = (u32*)take(S * 4);
     w.region_full = (u32*)take(S * kMaxBuckets * 4);
     w.bucket_full = (u32*)take(S * kMaxBuckets * 4);
     w.counts = (u32*)take(R * kMaxBuckets * 4);

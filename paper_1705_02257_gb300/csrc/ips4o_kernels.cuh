@@ -940,6 +940,7 @@ __device__ void prefix_sub(const Workspace<T>& ws, u32 j, u64* tmp64, u32* s_sbk
     const u32 word = __ballot_sync(0xffffffffu, no_blocks);
     if ((b & 31) == 0 && b < kMaxBuckets) ws.exhausted[(u64)j * 8 + (b >> 5)] = word;
     if (threadIdx.x == 0) {
+        ws.movers[j] = 0;
         for (u32 i = 0; i < ns; ++i) blocks += s_full[i];
         ws.subs[j].blocks_total = blocks;
     }
@@ -1077,6 +1078,7 @@ struct PermuteCfg {
     static constexpr int NCHT = BB / CHB;
     static constexpr int NCH = (NCHT + 31) / 32;
     static constexpr int MAX_MOVERS_PER_BUCKET = 128;
+    static constexpr int MAX_JOINS = 32;         // subproblems a CTA joins after its own groups
     // block buffers of the warps, then one copy of the subproblem's tables
     // shared by the CTA (all its warps move blocks of the same subproblem)
     static constexpr size_t off_buf = 0;                                          // E[NW][2][V][B]
@@ -1101,15 +1103,30 @@ __device__ __forceinline__ void load_sub_tables(const Workspace<T>& ws, u32 j, t
     for (int i = threadIdx.x; i <= kMaxBuckets; i += blockDim.x) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
 }
 
+// The first bucket at or after start (cyclically over the 256 bits) that the
+// exhausted bitmap exw does not mark; 0xffffffff when every bucket is marked.
+__device__ __forceinline__ u32 first_live_bucket(const u32 (&exw)[8], u32 start) {
+    for (u32 step = 0; step < 8 * 32;) {
+        const u32 c = (start + step) & 255u;
+        const u32 free_bits = ~exw[c >> 5] >> (c & 31);
+        if (free_bits) return c + (u32)(__ffs(free_bits) - 1);   // stays inside word c >> 5
+        step += 32 - (c & 31);
+    }
+    return 0xffffffffu;
+}
+
 // One mover group (a warp of V movers) of subproblem j: group gl of the
 // subproblem's groups, nmov movers in all (Section 4.2).  wbuf is the warp's
 // [2][V][b] block buffer; tree, spl, delim the subproblem's search tree,
-// splitters and delimiters in shared memory (load_sub_tables).
+// splitters and delimiters in shared memory (load_sub_tables).  A group that
+// joins a subproblem already being permuted (join) starts each mover on the
+// first bucket at or after its share that the exhausted bitmap does not
+// mark, so no mover starts with a claim on a bucket known to be used up.
 template <class T>
 __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Workspace<T>& ws, u32 j, u32 gl,
                                               u32 nmov, typename T::elem_t* wbuf, const typename T::key_t* tree,
                                               const typename T::key_t* spl, const u32* delim, u32 spin_limit,
-                                              u64& moved, u64& skipped, bool& failed) {
+                                              u64& moved, u64& skipped, bool& failed, bool join = false) {
     typedef typename T::elem_t E;
     typedef typename T::key_t K;
     typedef PermuteCfg<T> C;
@@ -1134,7 +1151,13 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
     u32 exw[8];
 #pragma unroll
     for (int w8 = 0; w8 < 8; ++w8) exw[w8] = 0;
-    bool exw_valid = false;
+    if (join && is_mover) {
+#pragma unroll
+        for (int w8 = 0; w8 < 8; ++w8) exw[w8] = ld_relaxed(&exh[w8]);
+        const u32 np = first_live_bucket(exw, prim);
+        if (np == 0xffffffffu || np >= nb) done = true;
+        else prim = np;
+    }
     for (;;) {
         if (!__any_sync(0xffffffffu, !done) || failed) break;
         // ---- one claim per active mover.  The read claims of the lanes that
@@ -1268,27 +1291,85 @@ __device__ __forceinline__ void permute_group(typename T::elem_t* arr, const Wor
             if (exd) {
 #pragma unroll
                 for (int w8 = 0; w8 < 8; ++w8) exw[w8] = ld_relaxed(&exh[w8]);
-                exw_valid = true;
                 // first non-exhausted bucket after prim, cyclically
-                u32 np = 0xffffffffu;
-                for (u32 step = 1; step <= 8 * 32 && np == 0xffffffffu; ) {
-                    const u32 c = (prim + step) & 255u;
-                    const u32 free_bits = ~exw[c >> 5] >> (c & 31);
-                    if (free_bits) {
-                        const u32 cand = c + (u32)(__ffs(free_bits) - 1);
-                        // a candidate past the end of this word wraps at bit 31
-                        np = cand;
-                    } else {
-                        step += 32 - (c & 31);
-                    }
-                }
+                const u32 np = first_live_bucket(exw, prim + 1u);
                 if (np == 0xffffffffu) done = true;
                 else if (IPS4O_GUARD(ws.ctr, np < nb, np, nb)) prim = np;
                 else { failed = true; done = true; }
             }
         }
-        (void)exw_valid;
     }
+}
+
+constexpr u32 kJoinNone = 0xffffffffu;
+constexpr u32 kJoinRetry = 0xfffffffeu;
+
+// For a CTA of k_permute whose own groups are done: the subproblem of the
+// round with the most estimated unprocessed blocks per CTA working on it
+// (r_i - w_i + 1 summed over 8 sampled buckets, scaled to all buckets),
+// kJoinNone when none has 4 blocks per mover left, kJoinRetry when the
+// chosen one filled up meanwhile.  Thread 0 counts the CTA in ws.movers; all
+// threads receive the index.  s_red: NW + 1 words of shared memory.
+//
+// The cap on CTAs per subproblem also bounds how far r_i may fall below
+// w_i - 1: every mover fails a read claim on a bucket at most once per
+// group, and a group that joins starts its movers only on buckets the
+// exhausted bitmap does not mark; a subproblem is joined only while all movers
+// of the grid together with its own cap stay below the bias kRBias.
+template <class T>
+__device__ u32 pick_join(const Workspace<T>& ws, u32 nsub, u32 G, u32 salt, u64* s_red) {
+    typedef PermuteCfg<T> C;
+    constexpr int TPB = C::TPB, NW = C::NW;
+    constexpr u32 MOV = (u32)NW * C::V;
+    u64 best = 0;                                // score << 32 | tie-break << 16 | subproblem
+    for (u32 i = threadIdx.x; i < nsub; i += TPB) {
+        const u32 nb = ws.subs[i].nbuckets;
+        if (nb == 0 || nb > (u32)kMaxBuckets || ws.subs[i].blocks_total == 0) continue;
+        const u64 cap_b = ((u64)nb * C::MAX_MOVERS_PER_BUCKET + MOV - 1) / MOV;
+        if (((u64)G + cap_b) * MOV >= kRBias) continue;
+        const u32 act = ld_relaxed(&ws.movers[i]);
+        if (act >= cap_b) continue;
+        const u64* wr = ws.wr + (u64)i * kMaxBuckets;
+        u64 rem = 0;
+#pragma unroll
+        for (u32 q = 0; q < 8; ++q) {
+            const u64 x = ld_relaxed64(&wr[(q * nb) >> 3]);
+            const long long d = pk_r(x) - pk_w(x) + 1;
+            rem += d > 0 ? (u64)d : 0ull;
+        }
+        rem = rem * nb / 8;
+        if (rem < 4ull * MOV) continue;
+        u64 score = rem * 256 / (act + 1);
+        score = score < 0xffffffffull ? score : 0xffffffffull;
+        const u64 tie = mix64(((u64)salt << 32) | i) >> 48;
+        const u64 key = (score << 32) | (tie << 16) | i;
+        best = key > best ? key : best;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const u64 y = __shfl_xor_sync(0xffffffffu, best, o);
+        best = y > best ? y : best;
+    }
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        u64 b = s_red[0];
+        for (int w = 1; w < NW; ++w) b = s_red[w] > b ? s_red[w] : b;
+        u32 j = kJoinNone;
+        if (b != 0) {
+            j = (u32)(b & 0xffffu);
+            const u32 cap_b = (ws.subs[j].nbuckets * (u32)C::MAX_MOVERS_PER_BUCKET + MOV - 1) / MOV;
+            if (atomicAdd(&ws.movers[j], 1u) >= cap_b) {
+                atomicSub(&ws.movers[j], 1u);
+                j = kJoinRetry;
+            }
+        }
+        s_red[NW] = j;
+    }
+    __syncthreads();
+    const u32 j = (u32)s_red[NW];
+    __syncthreads();                             // s_red is read before the next pick writes it
+    return j;
 }
 
 template <class T>
@@ -1305,8 +1386,11 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     if (ws.ls) nsub = ws.ls->nsub;                  // device-planned round
     const u32 G = gridDim.x;                      // CTAs in the grid
     constexpr u32 MOV = (u32)NW * V;              // movers of one CTA
-    // CTAs per subproblem, in proportion to its full blocks; the warps of a
-    // CTA all work on one subproblem and share its tables
+    // CTAs per subproblem, in proportion to its full blocks (rounded down,
+    // then one more for each of the first subproblems, the largest, until the
+    // grid is used up), so that one wave of groups covers the round when it
+    // has no more subproblems than CTAs; the warps of a CTA all work on one
+    // subproblem and share its tables
     u64 mine = 0;
     for (u32 i = threadIdx.x; i < nsub; i += TPB) mine += ws.subs[i].blocks_total;
     if (threadIdx.x == 0) s_misc[0] = 0;
@@ -1316,28 +1400,46 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     const u64 total = s_misc[0];
     {
         constexpr int PER = 1024 / TPB;
-        u32 gv[PER], sum = 0;
+        u32 gv[PER], cap[PER], sum = 0, below = 0;
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
             const u32 i = threadIdx.x * PER + q;
             gv[q] = 0;
+            cap[q] = 0;
             if (i < nsub && total > 0) {
                 const SubDesc& sd = ws.subs[i];
                 const u64 bl = sd.blocks_total;
                 if (bl > 0) {
-                    u64 x = (bl * (u64)G + total - 1) / total;
+                    u64 x = bl * (u64)G / total;
                     const u64 cap_b = ((u64)sd.nbuckets * C::MAX_MOVERS_PER_BUCKET + MOV - 1) / MOV;
                     const u64 cap_k = (bl + MOV - 1) / MOV;
                     const u64 cap_r = kMaxReadersPerSub / NW;
-                    x = x < cap_b ? x : cap_b;
-                    x = x < cap_k ? x : cap_k;
-                    x = x < cap_r ? x : cap_r;
+                    u64 c = cap_b < cap_k ? cap_b : cap_k;
+                    c = c < cap_r ? c : cap_r;
+                    c = c < 1 ? 1 : c;
+                    x = x < c ? x : c;
                     gv[q] = (u32)(x < 1 ? 1 : x);
+                    cap[q] = (u32)c;
                 }
             }
             sum += gv[q];
+            below += gv[q] < cap[q] ? 1u : 0u;
         }
-        u32 tot;
+        u32 tot, nbelow;
+        block_exclusive_scan<u32>(sum, (u32*)(s_misc + 1), &tot);
+        __syncthreads();                          // the scan's scratch is read before it is reused
+        u32 rank = block_exclusive_scan<u32>(below, (u32*)(s_misc + 1), &nbelow);
+        const u32 spare = tot < G ? G - tot : 0u;
+        sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            if (gv[q] < cap[q]) {
+                if (rank < spare) ++gv[q];
+                ++rank;
+            }
+            sum += gv[q];
+        }
+        __syncthreads();
         u32 p = block_exclusive_scan<u32>(sum, (u32*)(s_misc + 1), &tot);
 #pragma unroll
         for (int q = 0; q < PER; ++q) {
@@ -1354,7 +1456,7 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
     K* spl = (K*)(smem_raw + C::off_spl);
     u32* delim = (u32*)(smem_raw + C::off_delim);
     u64 moved = 0, skipped = 0;
-    bool failed = false;
+    bool failed = false, cta_failed = false;
     for (u32 g = blockIdx.x; g < GT; g += G) {
         u32 lo = 0, hi = nsub;
         while (hi - lo > 1) { u32 mid = (lo + hi) >> 1; if (s_gpre[mid] <= g) lo = mid; else hi = mid; }
@@ -1363,10 +1465,28 @@ __global__ void __launch_bounds__(PermuteCfg<T>::TPB, PermuteCfg<T>::MIN_CTAS)
         const u32 nmov = (s_gpre[j + 1] - s_gpre[j]) * MOV;
         __syncthreads();                          // the previous group is done with the tables
         load_sub_tables<T>(ws, j, tree, spl, delim);
+        if (threadIdx.x == 0) atomicAdd(&ws.movers[j], 1u);
         __syncthreads();
         permute_group<T>(arr, ws, j, cl * NW + warp, nmov, wbuf, tree, spl, delim, spin_limit, moved, skipped,
                          failed);
-        if (__syncthreads_or(failed)) break;
+        cta_failed = __syncthreads_or(failed) != 0;
+        if (threadIdx.x == 0) atomicSub(&ws.movers[j], 1u);
+        if (cta_failed) break;
+    }
+    // A CTA whose groups are done joins a subproblem whose permutation still
+    // has unprocessed blocks (the movers of a subproblem need not start
+    // together), so that the round does not wait on the subproblems whose
+    // CTAs had the most blocks each.
+    for (u32 round = 0; round < C::MAX_JOINS && !cta_failed; ++round) {
+        const u32 j = pick_join<T>(ws, nsub, G, blockIdx.x * C::MAX_JOINS + round, s_misc + 1);
+        if (j == kJoinNone) break;
+        if (j == kJoinRetry) continue;
+        load_sub_tables<T>(ws, j, tree, spl, delim);
+        __syncthreads();
+        permute_group<T>(arr, ws, j, (u32)warp, MOV, wbuf, tree, spl, delim, spin_limit, moved, skipped, failed,
+                         true);
+        cta_failed = __syncthreads_or(failed) != 0;
+        if (threadIdx.x == 0) atomicSub(&ws.movers[j], 1u);
     }
     if (moved) atomicAdd(&ws.ctr->blocks_moved, moved);
     if (skipped) atomicAdd(&ws.ctr->blocks_skipped, skipped);
