@@ -404,27 +404,43 @@ __device__ void cta_sort(typename T::elem_t* g, u32 m, unsigned char* smem, type
     __syncthreads();
 }
 
-// Base-case tasks (buckets or whole small inputs): a persistent grid takes
-// tasks i = blockIdx.x, blockIdx.x + gridDim.x, ... of the list; the count is
-// read from device memory, so the launch does not depend on the host.  With
-// out, each sorted bucket goes to the same range of out instead of arr.
-// With a size window (min_excl, max_incl], only the tasks of that size are
-// sorted (a list of tasks of all size classes, one launch per class).
+// Base-case tasks (buckets or whole small inputs): a persistent grid whose
+// CTAs take the next entry of the list from a counter (ctr->base_next)
+// whenever they are free, so that they finish together whatever the sizes;
+// the count is read from device memory, so the launch does not depend on the
+// host.  The last CTA to take its last entry sets the counter back to zero
+// for the next launch (every CTA has then made its last claim: its claim
+// returned before it counted itself in ctr->base_done).  With out, each
+// sorted bucket goes to the same range of out instead of arr.  With a size
+// window (min_excl, max_incl], only the tasks of that size are sorted (a list
+// of tasks of all size classes, one launch per class).
 template <class T, class C>
 __global__ void __launch_bounds__(C::TPB, (C::TPB <= 256 ? 4 : (C::TPB <= 512 ? 2 : 1)))
     k_base(typename T::elem_t* arr, const Task* tasks, const u32* count, ChunkCounters* ctr,
            typename T::elem_t* out = nullptr, u64 min_excl = 0, u64 max_incl = ~0ull) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ u32 s_task;
     const u32 n = *count;
     u32 mine = 0;
-    for (u32 i = blockIdx.x; i < n; i += gridDim.x) {
+    for (;;) {
+        if (threadIdx.x == 0) s_task = atomicAdd(&ctr->base_next, 1u);
+        __syncthreads();
+        const u32 i = s_task;
+        __syncthreads();
+        if (i >= n) break;
         const Task t = tasks[i];
         if (t.n <= min_excl || t.n > max_incl) continue;
         if (!IPS4O_GUARD(ctr, t.n <= (u64)C::CAP, t.n, C::CAP)) continue;
         cta_sort<T, C>(arr + t.begin, (u32)t.n, smem_raw, out ? out + t.begin : nullptr);
         ++mine;
     }
-    if (threadIdx.x == 0 && mine) atomicAdd(&ctr->base_buckets, (u64)mine);
+    if (threadIdx.x == 0) {
+        if (mine) atomicAdd(&ctr->base_buckets, (u64)mine);
+        if (atomicAdd(&ctr->base_done, 1u) == gridDim.x - 1) {
+            ctr->base_next = 0;
+            ctr->base_done = 0;
+        }
+    }
 }
 
 }  // namespace ips4o

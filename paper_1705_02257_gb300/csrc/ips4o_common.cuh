@@ -233,6 +233,8 @@ struct ChunkCounters {
     u32 status;         // error bits
     u32 guard_line;     // first failed bounds guard: source line (0 = none)
     u32 guard_hits;     // number of failed bounds guards
+    u32 base_next;      // base case: next entry of the task list (zero between launches)
+    u32 base_done;      // base case: CTAs of the launch that have taken their last entry
     u32 pad;
     u64 guard_a, guard_b;   // operands of the first failed guard
     u32 base_small;     // base-case tasks of the small size class
