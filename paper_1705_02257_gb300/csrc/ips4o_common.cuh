@@ -470,6 +470,28 @@ constexpr int kLutCells = 4096;
 constexpr int kLutBits = 12;                    // log2(kLutCells)
 constexpr int kLutMinLevels = 5;                // smaller trees keep the descent
 
+// Index of the lowest set bit of x plus one (0 for x == 0).
+__host__ __device__ __forceinline__ int ffs32(u32 x) {
+#ifdef __CUDA_ARCH__
+    return __ffs((int)x);
+#else
+    return __builtin_ffs((int)x);
+#endif
+}
+
+// The first bucket at or after start (cyclically over the 256 bits) that the
+// exhausted bitmap exw of the block permutation does not mark; 0xffffffff
+// when every bucket is marked.
+__host__ __device__ __forceinline__ u32 first_live_bucket(const u32 (&exw)[8], u32 start) {
+    for (u32 step = 0; step < 8 * 32;) {
+        const u32 c = (start + step) & 255u;
+        const u32 free_bits = ~exw[c >> 5] >> (c & 31);
+        if (free_bits) return c + (u32)(ffs32(free_bits) - 1);   // stays inside word c >> 5
+        step += 32 - (c & 31);
+    }
+    return 0xffffffffu;
+}
+
 // Bit length of x (0 for x == 0).
 __host__ __device__ __forceinline__ u32 bitlen64(u64 x) {
 #ifdef __CUDA_ARCH__

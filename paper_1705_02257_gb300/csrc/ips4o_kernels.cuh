@@ -1103,18 +1103,6 @@ __device__ __forceinline__ void load_sub_tables(const Workspace<T>& ws, u32 j, t
     for (int i = threadIdx.x; i <= kMaxBuckets; i += blockDim.x) delim[i] = ws.delim[(u64)j * (kMaxBuckets + 1) + i];
 }
 
-// The first bucket at or after start (cyclically over the 256 bits) that the
-// exhausted bitmap exw does not mark; 0xffffffff when every bucket is marked.
-__device__ __forceinline__ u32 first_live_bucket(const u32 (&exw)[8], u32 start) {
-    for (u32 step = 0; step < 8 * 32;) {
-        const u32 c = (start + step) & 255u;
-        const u32 free_bits = ~exw[c >> 5] >> (c & 31);
-        if (free_bits) return c + (u32)(__ffs(free_bits) - 1);   // stays inside word c >> 5
-        step += 32 - (c & 31);
-    }
-    return 0xffffffffu;
-}
-
 // One mover group (a warp of V movers) of subproblem j: group gl of the
 // subproblem's groups, nmov movers in all (Section 4.2).  wbuf is the warp's
 // [2][V][b] block buffer; tree, spl, delim the subproblem's search tree,

@@ -52,3 +52,20 @@ def test_noalloc_scratch_holds_every_accepted_sort(tmp_path):
     assert r.returncode == 0, r.stdout + r.stderr
     r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout + r.stderr
+
+
+def test_exhausted_bitmap_search_equals_bit_by_bit(tmp_path):
+    """first_live_bucket, the block permutation's search for the next bucket
+    with unprocessed blocks, against testing the bits one at a time for
+    every start and many bitmaps (tests/host/bitmap_check.cu, host only)."""
+    nvcc = _nvcc()
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    exe = str(tmp_path / "bitmap_check")
+    cmd = [nvcc, "-std=c++17", "-O2", "-gencode", "arch=compute_103a,code=sm_103a", "-I", CSRC,
+           os.path.join(HERE, "host", "bitmap_check.cu"), "-o", exe]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.startswith("ok "), r.stdout + r.stderr
+    assert int(r.stdout.split()[1]) > 1_000_000
